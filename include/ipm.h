@@ -1,0 +1,205 @@
+/*
+ * ipm.h -- C ABI of libipm: the interior point method of Pearson, Porcelli and
+ * Stoll, "Interior point methods and preconditioning for PDE-constrained
+ * optimization problems involving sparsity terms" (2018), on one GB300 GPU.
+ *
+ * Problem (Section 1, (pb)-(boxs); discrete form (pb_fe)+(boxvector), Section 2):
+ *   min  1/2 ||y - y_d||^2_{L2} + alpha/2 ||u||^2_{L2} + beta ||u||_{L1}
+ *   s.t. -Lap y = u + f   (or -eps Lap y + w . grad y = u + f, SUPG-stabilised)
+ *        y = g on the boundary,  u_a <= u <= u_b,  y_a <= y <= y_b,
+ * on the unit square (cube) with Q1 elements on a uniform grid of n nodes per
+ * direction. The unknowns are the interior nodes for y, u and p alike.
+ * The solver runs Algorithm A.1 (Appendix); each Newton system
+ * (NewtonSystem, Section 3) is solved by MINRES with the block-diagonal
+ * preconditioner P_D or by (flexible) GMRES with the block-triangular P_T
+ * (Section 4), entirely in CUDA kernels.
+ *
+ * Conventions for every function below:
+ *   - Nodal arrays are full grids of n^d doubles, boundary included, C order
+ *     with x fastest ("[z][y][x]"). Host pointers unless the name says _device.
+ *   - The library copies inputs at call time; the caller keeps ownership of
+ *     its buffers. The solver owns all device memory it allocates until
+ *     ipm_destroy.
+ *   - Every int-returning function returns IPM_OK (0) or one of the IPM_E*
+ *     codes; ipm_last_error gives a message. On error nothing is written to
+ *     output buffers unless stated.
+ *   - A solver is not thread-safe; use one solver per host thread.
+ */
+#ifndef IPM_H
+#define IPM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ipm_solver ipm_solver; /* opaque */
+
+enum {
+  IPM_OK = 0,
+  IPM_EINVAL = 1,     /* bad argument: grid, alpha <= 0, beta < 0, bounds violating u_a < 0 < u_b */
+  IPM_ENOMEM = 2,     /* device allocation failed */
+  IPM_ENOTCONV = 3,   /* iteration cap hit; the last iterate is still retrievable */
+  IPM_EBREAKDOWN = 4, /* Krylov breakdown or non-finite values */
+  IPM_ETIMEOUT = 5,   /* wall-clock limit of ipm_options.time_limit_s reached */
+  IPM_ECUDA = 6,      /* CUDA runtime error */
+  IPM_ESTATE = 7      /* call out of order (e.g. solve before set_data, get before solve) */
+};
+
+/* Grid: dim = 2 or 3, n[0] = n[1] (= n[2]) = nodes per direction incl. boundary,
+ * n = 2^k + 1 with k >= 1 (the multigrid hierarchy halves the mesh down to 3 nodes). */
+typedef struct {
+  int dim;
+  int n[3];
+} ipm_grid;
+
+/* State equation: Poisson (Sections 5.1) or convection-diffusion with SUPG
+ * (Section 5.2; 2D only) with diffusion eps and the recirculating wind
+ * w = (2 x2 (1 - x1^2), -2 x1 (1 - x2^2)) (wind = 0). */
+typedef enum { IPM_POISSON = 0, IPM_CONVDIFF_SUPG = 1 } ipm_pde_kind;
+typedef struct {
+  int kind;
+  double eps;
+  int wind;
+} ipm_pde;
+
+/* Bounds (Section 1, (box), (boxs)). Scalars, or nodal arrays when the pointer
+ * is non-NULL (full grid, only interior entries are read). The control bounds
+ * must satisfy u_a < 0 < u_b (the paper's sign convention) and may be +-INFINITY;
+ * y_a = -INFINITY / y_b = +INFINITY mark an absent state bound. */
+typedef struct {
+  double ua, ub, ya, yb;
+  const double *ua_v, *ub_v, *ya_v, *yb_v;
+} ipm_bounds;
+
+enum { IPM_PREC_FP64 = 0, IPM_PREC_MIXED = 1 };
+enum { IPM_KRYLOV_MINRES_PD = 0, IPM_KRYLOV_GMRES_PT = 1 };
+enum { IPM_STOP_PAPER = 0, IPM_STOP_KKT = 1, IPM_STOP_FIXED = 2 };
+
+/* Solver options; ipm_default_options fills the paper's values (Section 5):
+ * alpha0 = 0.995, eps_p = eps_d = eps_c = 1e-6, sigma = 0.2, mu0 = 1,
+ * Krylov tolerance 1e-10 (relative unpreconditioned residual), 20 Chebyshev
+ * steps, 3 V-cycles with 5 pre- and 5 post-smoothing steps.
+ *   precision: IPM_PREC_FP64 everywhere, or IPM_PREC_MIXED (Chebyshev and
+ *              multigrid in FP32; Krylov recurrences, operator and IPM in FP64;
+ *              the Krylov method is then flexible GMRES).
+ *   krylov:    IPM_KRYLOV_MINRES_PD (MINRES + P_D) or IPM_KRYLOV_GMRES_PT
+ *              (GMRES + P_T, right-preconditioned, flexible form).
+ *   stop:      IPM_STOP_PAPER: ||xi_p|| <= eps_p, ||xi_d|| <= eps_d, ||xi_c|| <= eps_c
+ *              (Algorithm A.1); IPM_STOP_KKT: kkt_rel <= kkt_tol; IPM_STOP_FIXED:
+ *              exactly fixed_iters IPM iterations.
+ *   kkt_rel = max( ||xi_p|| / (1 + ||f|| + ||M y_d||), ||xi_d|| / (1 + ||M y_d|| + beta ||D 1||),
+ *                  mean complementarity product / (1 + |Q(y, z)|) ).                       */
+typedef struct {
+  int precision;
+  int krylov;
+  int stop;
+  double sigma, alpha0, eps_p, eps_d, eps_c, mu0, kkt_tol, krylov_tol;
+  int cheb_steps, vcycles, smooth_pre, smooth_post;
+  int max_ipm, max_krylov, restart, fixed_iters;
+  double time_limit_s; /* <= 0: none */
+} ipm_options;
+
+typedef struct {
+  int status;             /* IPM_OK, IPM_ENOTCONV, ... */
+  int ipm_iters;          /* Newton steps taken */
+  int krylov_iters_total; /* Krylov iterations over all Newton steps */
+  double kkt_rel, xi_p, xi_d, xi_c, mu;
+  double krylov_relres_max; /* worst final relative residual of the Newton solves */
+  double seconds;           /* wall time of ipm_solve */
+} ipm_report;
+
+void ipm_default_options(ipm_options* opt);
+
+/* Create a solver for one problem; allocates all device memory on the current
+ * CUDA device. beta >= 0, alpha > 0. On success *out owns the solver. */
+int ipm_create(const ipm_grid* grid, const ipm_pde* pde, double alpha, double beta,
+               const ipm_bounds* bounds, ipm_solver** out);
+
+/* Use an existing CUDA stream (cudaStream_t passed as void*; NULL = the
+ * solver's own stream). All device work of later calls is ordered on it. */
+int ipm_set_stream(ipm_solver* s, void* cuda_stream);
+
+/* Problem data (Section 1): desired state y_d, source f, Dirichlet data g
+ * (boundary entries of g are used). Host arrays of n^d doubles; NULL = zero. */
+int ipm_set_data(ipm_solver* s, const double* yd, const double* f, const double* g);
+/* Same, from device arrays of n^d doubles (no host copy). */
+int ipm_set_data_device(ipm_solver* s, const double* yd, const double* f, const double* g);
+
+/* Run Algorithm A.1 from the central-path start. opt NULL = defaults; rep may be
+ * NULL. Returns IPM_OK or IPM_ENOTCONV (iterate still available), or an error. */
+int ipm_solve(ipm_solver* s, const ipm_options* opt, ipm_report* rep);
+
+/* Results after ipm_solve into caller-owned buffers of len = n^d doubles:
+ * state y (boundary = g), control u = w - v (boundary 0), adjoint p (boundary 0). */
+int ipm_get_state(const ipm_solver* s, double* y, size_t len);
+int ipm_get_control(const ipm_solver* s, double* u, size_t len);
+int ipm_get_adjoint(const ipm_solver* s, double* p, size_t len);
+/* Same into device buffers of n^d doubles (enqueued on the solver's stream). */
+int ipm_get_state_device(const ipm_solver* s, double* y, size_t len);
+int ipm_get_control_device(const ipm_solver* s, double* u, size_t len);
+int ipm_get_adjoint_device(const ipm_solver* s, double* p, size_t len);
+
+/* Per-iteration history of the last solve: rows of 10 doubles
+ * (k, mu, ||xi_p||, ||xi_d||, ||xi_c||, kkt_rel, alpha_P, alpha_D, krylov_iters,
+ *  krylov_relres); row 0 is the starting point. Writes min(max_rows, rows). */
+int ipm_get_history(const ipm_solver* s, double* rows, int max_rows, int* n_rows);
+
+void ipm_destroy(ipm_solver* s);
+/* Total number of CUDA kernels this library has launched since it was loaded
+ * (all solvers, all threads). */
+long long ipm_launch_count(void);
+/* Sampled timing of the finest-level multigrid smoother (the dominant kernel):
+ * enable = 1 starts recording a CUDA event pair around every `every`-th launch on
+ * the solver's stream (and clears earlier samples); enable = 0 stops.
+ * ipm_profile_read returns the summed event time of the sampled launches, their
+ * number, and the algorithmic bytes one launch moves (read x, b, m, jinv and write x
+ * once per unknown, in the precision of the mixed path: 4-byte values). */
+int ipm_profile_smoother(ipm_solver* s, int enable, int every);
+int ipm_profile_read(ipm_solver* s, double* total_ms, long long* launches, double* bytes_per_launch);
+const char* ipm_strerror(int code);
+const char* ipm_last_error(const ipm_solver* s);
+
+/* ---------------------------------------------------------------------------
+ * Component entry points: one stage of the hot path on device buffers, for
+ * checking kernels in isolation. Nodal device arrays of n^d doubles (dense,
+ * boundary included, x fastest); "4-field" arrays hold (y, w, v, p) blocks of
+ * n^d each, back to back. Boundary entries of inputs are ignored, outputs get
+ * zero boundaries. They use the solver's grid, operator and parameters.
+ * --------------------------------------------------------------------------- */
+
+/* out = calA x with calA the matrix of (NewtonSystem) for the given diagonals
+ * Theta_y, Theta_w, Theta_v (Section 3). x, out: 4-field. */
+int ipm_newton_apply_device(ipm_solver* s, const double* theta_y, const double* theta_w,
+                            const double* theta_v, const double* x, double* out);
+
+/* z = P^{-1} r for P_D (triangular = 0) or P_T (triangular = 1) built from the
+ * given diagonals (Section 4), with the options' Chebyshev / multigrid settings
+ * and precision. r, z: 4-field. */
+int ipm_precond_apply_device(ipm_solver* s, const ipm_options* opt, int triangular,
+                             const double* theta_y, const double* theta_w, const double* theta_v,
+                             const double* r, double* z);
+
+/* x = Chebyshev_k(M + Theta_y)^{-1} b: k steps of Chebyshev semi-iteration with
+ * the Jacobi splitting D_M + Theta_y (Section 4.1), FP64. b, x: nodal. */
+int ipm_chebyshev_device(ipm_solver* s, int steps, const double* theta_y, const double* b,
+                         double* x);
+
+/* x = V-cycle approximation of (L + diag(m))^{-1} b (transpose = 1: (L^T + diag(m))^{-1}),
+ * `cycles` V-cycles from x = 0 with the options' smoothing counts, FP64. m, b, x: nodal. */
+int ipm_vcycle_device(ipm_solver* s, const ipm_options* opt, int transpose, const double* m,
+                      const double* b, double* x);
+
+/* Newton direction of Algorithm A.1 from a given iterate: loads (y, w, v, p and
+ * the six multipliers; 10 nodal arrays, NULL multipliers for absent bounds), forms
+ * Theta, M_hat and the right-hand side at barrier parameter mu, and solves
+ * (NewtonSystem) with the options' Krylov method. dx: 4-field output. Also
+ * returns the Krylov iteration count and final relative residual when non-NULL. */
+int ipm_newton_step_device(ipm_solver* s, const ipm_options* opt, const double* const* iterate,
+                           double mu, double* dx, int* iters, double* relres);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IPM_H */

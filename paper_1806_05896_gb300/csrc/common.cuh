@@ -1,0 +1,222 @@
+// Shared device-side definitions: grid layout, Q1 stencils, reductions.
+//
+// Layout: every nodal field lives on the full uniform grid of the unit square
+// (cube), boundary nodes included, x fastest, rows padded to `pitch` elements
+// (a multiple of 32) so that rows start on 128-byte (FP32) / 256-byte (FP64)
+// boundaries. Boundary and padding entries of vectors the Krylov solvers see
+// are kept at zero, so whole-field reductions equal sums over the unknowns.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#define IPM_HD __host__ __device__ __forceinline__
+#define IPM_D __device__ __forceinline__
+
+struct GridDesc {
+  int dim;          // 2 or 3
+  int n;            // nodes per direction, boundary included
+  int pitch;        // elements per row
+  long long plane;  // elements per z-plane (pitch * n)
+  long long field;  // elements per field (plane for 2D, plane * n for 3D)
+  double h;         // mesh size 1/(n-1)
+};
+
+IPM_HD long long node_index(const GridDesc& g, int i, int j, int k) {
+  return (long long)k * g.plane + (long long)j * g.pitch + i;
+}
+
+inline GridDesc make_grid(int dim, int n) {
+  GridDesc g;
+  g.dim = dim;
+  g.n = n;
+  g.pitch = (n + 31) / 32 * 32;
+  g.plane = (long long)g.pitch * n;
+  g.field = dim == 2 ? g.plane : g.plane * n;
+  g.h = 1.0 / (n - 1);
+  return g;
+}
+
+// Launch shape for one thread per interior node: x along rows, y across rows,
+// z over interior planes (3D).
+inline dim3 interior_block() { return dim3(32, 8, 1); }
+inline dim3 interior_grid(const GridDesc& g) {
+  int m = g.n - 2;
+  return dim3((m + 31) / 32, (m + 7) / 8, g.dim == 3 ? m : 1);
+}
+
+// Maps the calling thread to an interior node; returns false for threads past the edge.
+IPM_D bool interior_node(const GridDesc& g, int& i, int& j, int& k, long long& c) {
+  i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+  k = g.dim == 3 ? 1 + (int)blockIdx.z : 0;
+  if (i > g.n - 2 || j > g.n - 2) return false;
+  c = node_index(g, i, j, k);
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Q1 stencils on the uniform grid (interior rows of the Galerkin matrices).
+// Mass:      M = M1 (x) M1 [(x) M1],  M1 = (h/6)[1 4 1]
+// Stiffness: 2D  (1/3)[8 at centre, -1 at the 8 neighbours]  (independent of h)
+//            3D  h [8/3 centre, 0 faces, -1/6 edges, -1/12 corners]
+// Diagonals: D_M = (2h/3)^d;  stiffness diagonal 8/3 (2D), 8h/3 (3D).
+// ---------------------------------------------------------------------------
+// Generic forms take a load functor f(index) -> T, so that e.g. M(w - v)
+// forms the difference before the stencil sum.
+template <typename T, typename F>
+IPM_D T row141(const F& f, long long c) {
+  return f(c - 1) + T(4) * f(c) + f(c + 1);
+}
+template <typename T, typename F>
+IPM_D T row111(const F& f, long long c) {
+  return f(c - 1) + f(c) + f(c + 1);
+}
+// Mass action without the h^d/6^d factor.
+template <typename T, typename F>
+IPM_D T mass2_raw(const F& f, long long c, int p) {
+  return row141<T>(f, c - p) + T(4) * row141<T>(f, c) + row141<T>(f, c + p);
+}
+template <typename T, typename F>
+IPM_D T mass3_raw(const F& f, long long c, int p, long long pl) {
+  return mass2_raw<T>(f, c - pl, p) + T(4) * mass2_raw<T>(f, c, p) + mass2_raw<T>(f, c + pl, p);
+}
+// 2D stiffness: (8 x_c - sum of 8 neighbours)/3 = 3 x_c - (3x3 box sum)/3.
+template <typename T, typename F>
+IPM_D T stiff2(const F& f, long long c, int p) {
+  T box = row111<T>(f, c - p) + row111<T>(f, c) + row111<T>(f, c + p);
+  return T(3) * f(c) - box * T(1.0 / 3.0);
+}
+// 3D stiffness without the factor h: 8/3 x_c - (1/6) edges - (1/12) corners.
+template <typename T, typename F>
+IPM_D T stiff3_raw(const F& f, long long c, int p, long long pl) {
+  T e = f(c - p - 1) + f(c - p + 1) + f(c + p - 1) + f(c + p + 1);
+  T cor = T(0);
+#pragma unroll
+  for (int s = -1; s <= 1; s += 2) {
+    long long cc = c + s * pl;
+    e += f(cc - 1) + f(cc + 1) + f(cc - p) + f(cc + p);
+    cor += f(cc - p - 1) + f(cc - p + 1) + f(cc + p - 1) + f(cc + p + 1);
+  }
+  return T(8.0 / 3.0) * f(c) - e * T(1.0 / 6.0) - cor * T(1.0 / 12.0);
+}
+
+template <typename T>
+struct Ld {  // plain load functor
+  const T* __restrict__ x;
+  IPM_D T operator()(long long i) const { return x[i]; }
+};
+template <typename T>
+struct LdDiff {  // a - b
+  const T* __restrict__ a;
+  const T* __restrict__ b;
+  IPM_D T operator()(long long i) const { return a[i] - b[i]; }
+};
+template <typename T, typename S>
+struct LdCvt {  // load S, convert to T
+  const S* __restrict__ x;
+  IPM_D T operator()(long long i) const { return (T)x[i]; }
+};
+
+template <typename T>
+struct Stencil {
+  int dim;
+  int p;
+  long long pl;
+  T mscale;  // h^d / 6^d
+  T kscale;  // 1 (2D) or h (3D)
+  template <typename F>
+  IPM_D T mass_f(const F& f, long long c) const {
+    return mscale * (dim == 2 ? mass2_raw<T>(f, c, p) : mass3_raw<T>(f, c, p, pl));
+  }
+  template <typename F>
+  IPM_D T stiff_f(const F& f, long long c) const {
+    return dim == 2 ? stiff2<T>(f, c, p) : kscale * stiff3_raw<T>(f, c, p, pl);
+  }
+  IPM_D T mass(const T* __restrict__ x, long long c) const { return mass_f(Ld<T>{x}, c); }
+  IPM_D T stiff(const T* __restrict__ x, long long c) const { return stiff_f(Ld<T>{x}, c); }
+};
+
+template <typename T>
+inline Stencil<T> make_stencil(const GridDesc& g) {
+  Stencil<T> s;
+  s.dim = g.dim;
+  s.p = g.pitch;
+  s.pl = g.plane;
+  s.mscale = g.dim == 2 ? T(g.h * g.h / 36.0) : T(g.h * g.h * g.h / 216.0);
+  s.kscale = g.dim == 2 ? T(1) : T(g.h);
+  return s;
+}
+
+inline double mass_diag(const GridDesc& g) {  // (2h/3)^d
+  double t = 2.0 * g.h / 3.0;
+  return g.dim == 2 ? t * t : t * t * t;
+}
+inline double lumped_mass(const GridDesc& g) {  // h^d
+  return g.dim == 2 ? g.h * g.h : g.h * g.h * g.h;
+}
+inline double stiff_diag(const GridDesc& g) {  // 8/3 (2D) or 8h/3 (3D)
+  return g.dim == 2 ? 8.0 / 3.0 : 8.0 * g.h / 3.0;
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic block reductions: fixed grid, fixed per-thread order, warp
+// shuffles, then one partial per block; a second kernel sums the partials in
+// block order. Results are bitwise reproducible run to run.
+// ---------------------------------------------------------------------------
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 304;  // 2 x 152 SMs
+
+template <typename T>
+IPM_D T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+IPM_D T warp_min(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+IPM_D int lin_tid() { return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z); }
+IPM_D int block_threads() { return blockDim.x * blockDim.y * blockDim.z; }
+IPM_D long long lin_block() {
+  return blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+}
+IPM_D long long num_blocks() { return (long long)gridDim.x * gridDim.y * gridDim.z; }
+
+// Sum over the block (any shape, multiple of 32 threads); result valid in
+// linear thread 0. `sh` needs (threads/32) entries. All threads must call.
+template <typename T>
+IPM_D T block_sum(T v, T* sh) {
+  int t = lin_tid();
+  int lane = t & 31, w = t >> 5, nw = block_threads() >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  T r = T(0);
+  if (w == 0) {
+    r = lane < nw ? sh[lane] : T(0);
+    r = warp_sum(r);
+  }
+  __syncthreads();
+  return r;
+}
+IPM_D double block_min(double v, double* sh) {
+  int t = lin_tid();
+  int lane = t & 31, w = t >> 5, nw = block_threads() >> 5;
+  v = warp_min(v);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 1e300;
+  if (w == 0) {
+    r = lane < nw ? sh[lane] : 1e300;
+    r = warp_min(r);
+  }
+  __syncthreads();
+  return r;
+}

@@ -1,0 +1,128 @@
+// Host-side launch wrappers for every device kernel of the library.
+//
+// All wrappers enqueue on the given stream and return immediately. Pointers
+// are device pointers to fields in the pitched full-grid layout of common.cuh.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include "common.cuh"
+
+// Number of kernel launches enqueued by this library since it was loaded.
+void count_launches(long long n);
+long long launches_total();
+
+// ----------------------------------------------------------------------------
+// Problem fields
+// ----------------------------------------------------------------------------
+struct IpmState {  // primal-dual iterate, FP64
+  double *y, *w, *v, *p;
+  double *lya, *lyb, *lwa, *lwb, *lva, *lvb;
+};
+struct IpmBounds {  // +-inf marks an absent bound; the lower bounds of w and v are 0
+  const double *ya, *yb, *zbw, *zbv;
+};
+struct IpmDiag {  // barrier diagonals and the Schur-approximation diagonal M_hat
+  double *thy, *thw, *thv, *mh;
+  float *thy32, *mh32;
+};
+// Elliptic operator L: Poisson stiffness (stencil == nullptr) or a stored
+// 9-point stencil per node (convection-diffusion), coef[o * field + node] =
+// L[node, node + offset_o], offsets o = (dy+1)*3 + (dx+1).
+struct OpL {
+  const double* coef;
+  const float* coef32;
+};
+struct IpmProblem {
+  double alpha, beta;
+  double dM;  // diag(M), (2h/3)^d
+  double d;   // lumped mass, h^d
+  const double *cy, *fvec;
+  OpL L;
+};
+
+// ----------------------------------------------------------------------------
+// k_ipm.cu
+// ----------------------------------------------------------------------------
+void launch_pack(const GridDesc& g, const double* dense, double* pitched, int mode, cudaStream_t s);
+void launch_unpack(const GridDesc& g, const double* pitched, const double* bnd, double* dense,
+                   cudaStream_t s);
+void launch_setup_data(const GridDesc& g, const double* yd, const double* f, const double* glift,
+                       OpL L, double* cy, double* fvec, cudaStream_t s);
+void launch_element_mass_form(const GridDesc& g, const double* yd, const double* glift,
+                              double* part, double* out, cudaStream_t s);
+void launch_setup_norms(const GridDesc& g, const double* cy, const double* fvec,
+                        const IpmBounds& b, double* part, double* out, cudaStream_t s);
+void launch_init_state(const GridDesc& g, const IpmBounds& b, IpmState st, double mu0,
+                       cudaStream_t s);
+void launch_prep(const GridDesc& g, const IpmProblem& pb, const IpmBounds& b, IpmState st,
+                 IpmDiag dg, double mu, double* rhs, int write32, cudaStream_t s);
+void launch_steplen(const GridDesc& g, const IpmBounds& b, IpmState st, const double* dx,
+                    double mu, double alpha0, double* part, double* sc, cudaStream_t s);
+void launch_update(const GridDesc& g, const IpmBounds& b, IpmState st, const double* dx,
+                   double mu, const double* sc, cudaStream_t s);
+void launch_residuals(const GridDesc& g, const IpmProblem& pb, const IpmBounds& b, IpmState st,
+                      double mu, double* part, double* out, cudaStream_t s);
+void launch_newton_apply(const GridDesc& g, const IpmProblem& pb, const IpmDiag& dg,
+                         const double* x, double* y, cudaStream_t s);
+void launch_reduce_cols(const double* part, long long nrows, int ncols, double* out,
+                        cudaStream_t s);
+long long interior_blocks(const GridDesc& g);
+
+// ----------------------------------------------------------------------------
+// k_precond.cu
+// ----------------------------------------------------------------------------
+template <typename T>
+void launch_cheb_init(const GridDesc& g, const double* b, const T* thy, double dM, double inv_theta,
+                      T* bT, T* x1, T* x0, cudaStream_t s);
+template <typename T, typename To>
+void launch_cheb_step(const GridDesc& g, const T* xc, const T* xp, const T* bT, const T* thy,
+                      double dM, double omega, double inv_theta, To* out, cudaStream_t s);
+void launch_zblock(const GridDesc& g, double adM, const double* rw, const double* rv,
+                   const double* thw, const double* thv, double* zw, double* zv, cudaStream_t s);
+template <typename T>
+void launch_coupling(const GridDesc& g, OpL L, const double* zy, const double* zw, const double* zv,
+                     const double* rp, int triangular, T* t, cudaStream_t s);
+template <typename T>
+void launch_mass_theta(const GridDesc& g, const T* x, const T* thy, T* out, cudaStream_t s);
+template <typename Ti, typename To>
+void launch_convert(const GridDesc& g, const Ti* x, To* y, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// k_mg.cu (geometric multigrid on L + diag(m), Galerkin transfer P^T / P)
+// ----------------------------------------------------------------------------
+template <typename T>
+void launch_mg_smooth(const GridDesc& g, OpL L, const T* xin, T* xout, const T* b, const T* m,
+                      const T* jinv, int zero_init, int transpose, cudaStream_t s);
+template <typename T>
+void launch_mg_residual(const GridDesc& g, OpL L, const T* x, const T* b, const T* m, T* r,
+                        int transpose, cudaStream_t s);
+template <typename T>
+void launch_mg_restrict(const GridDesc& gf, const GridDesc& gc, const T* rf, T* bc, cudaStream_t s);
+template <typename T>
+void launch_mg_prolong_add(const GridDesc& gf, const GridDesc& gc, const T* xc, T* xf,
+                           cudaStream_t s);
+template <typename T>
+void launch_mg_coarsest(const GridDesc& g, OpL L, const T* b, const T* m, T* x, cudaStream_t s);
+template <typename T>
+void launch_mg_jinv(const GridDesc& g, OpL L, const T* m, double omega, T* jinv, cudaStream_t s);
+template <typename T>
+void launch_mg_zero(const GridDesc& g, T* x, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// k_vec.cu (Krylov vector kernels over whole field blocks, deterministic)
+// ----------------------------------------------------------------------------
+void launch_multidot(const double* V, long long stride, int nv, const double* w, long long len,
+                     double* part, double* out, cudaStream_t s);
+void launch_axpy_multi(double* w, const double* V, long long stride, int nv, const double* coef,
+                       double sign, long long len, cudaStream_t s);
+void launch_scale(double* y, const double* x, const double* num, const double* den, int invert,
+                  long long len, cudaStream_t s);
+void launch_axpby(double* y, const double* x, double a, double b, long long len, cudaStream_t s);
+void launch_axpy_dev(double* y, const double* x, const double* a, double sign, long long len,
+                     cudaStream_t s);
+void launch_dot(const double* a, const double* b, long long len, double* part, double* out,
+                cudaStream_t s);
+void launch_lincomb3(double* y, double a, const double* x1, double b, const double* x2, double c,
+                     const double* x3, long long len, cudaStream_t s);
+void launch_mhat(const GridDesc& g, double alpha, double dM, const double* thy, const double* thw,
+                 const double* thv, double* mh, float* thy32, float* mh32, cudaStream_t s);

@@ -1,0 +1,1006 @@
+// Host orchestration of the interior point method (Algorithm A.1, Appendix)
+// with preconditioned Krylov solves of (NewtonSystem) (Sections 3-4), and the
+// C ABI declared in include/ipm.h. Every arithmetic step runs in the kernels of
+// k_*.cu; the host only sequences launches and reads back scalars.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ipm.h"
+#include "kernels.h"
+
+namespace {
+
+struct IpmError {
+  int code;
+  std::string msg;
+};
+
+#define CK(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      throw IpmError{IPM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+constexpr int kMaxRestart = 100;
+constexpr int kHistCols = 10;
+
+template <typename T>
+struct MGLevel {
+  GridDesc g;
+  T* x[2];
+  T* b;
+  T* r;
+  T* m;
+  T* jinv;
+};
+template <typename T>
+struct MGHier {
+  int nlev = 0;
+  MGLevel<T> lv[16];
+  int cur[16];
+};
+
+}  // namespace
+
+struct ipm_solver {
+  GridDesc g;
+  ipm_pde pde;
+  double alpha = 0, beta = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t own = nullptr;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+
+  IpmState st{};
+  double *ya = nullptr, *yb = nullptr, *zbw = nullptr, *zbv = nullptr;
+  double *cy = nullptr, *fvec = nullptr, *glift = nullptr;
+  IpmDiag dg{};
+  double *rhs = nullptr, *dx = nullptr, *ktmp = nullptr;
+  double *V = nullptr, *Z = nullptr;
+  int vcap = 0;
+  double* mr[14] = {};
+  double* cheb64[3] = {};
+  float* cheb32[3] = {};
+  MGHier<double> mg64;
+  MGHier<float> mg32;
+  double *part = nullptr, *dout = nullptr, *sc = nullptr, *kdev = nullptr;
+  long long part_rows = 0;
+  double* hbuf = nullptr;  // pinned
+  double* dense = nullptr; // n^d scratch for packing
+
+  // sampled CUDA-event timing of the finest-level smoother launches
+  bool prof_on = false;
+  int prof_every = 8;
+  long long prof_seen = 0;
+  std::vector<cudaEvent_t> prof_ev;
+  int prof_used = 0;
+  double prof_ms = 0.0;
+  long long prof_count = 0;
+
+  double c0 = 0, ncy = 0, nf = 0, nd = 0, nbounds = 0;
+  bool has_data = false, solved = false;
+  std::vector<double> hist;  // rows of kHistCols
+  std::string err;
+
+  long long F() const { return g.field; }
+  long long nn() const { return (long long)g.n * g.n * (g.dim == 3 ? g.n : 1); }
+  long long nI() const {
+    long long m = g.n - 2;
+    return g.dim == 3 ? m * m * m : m * m;
+  }
+
+  template <typename T>
+  T* alloc(long long count) {
+    void* p = nullptr;
+    size_t b = (size_t)count * sizeof(T);
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw IpmError{IPM_ENOMEM, "cudaMalloc of " + std::to_string(b) + " bytes failed"};
+    }
+    CK(cudaMemset(p, 0, b));
+    allocs.push_back(p);
+    bytes += b;
+    return (T*)p;
+  }
+  void prof_flush() {
+    if (prof_used == 0) return;
+    CK(cudaStreamSynchronize(stream));
+    for (int i = 0; i + 1 < prof_used; i += 2) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, prof_ev[i], prof_ev[i + 1]));
+      prof_ms += ms;
+      ++prof_count;
+    }
+    prof_used = 0;
+  }
+  // record an event pair around the next launch if this one is sampled
+  bool prof_begin() {
+    if (!prof_on || (prof_seen++ % prof_every) != 0) return false;
+    if (prof_used + 2 > (int)prof_ev.size()) prof_flush();
+    if (prof_ev.size() < 512) {
+      while (prof_ev.size() < 512) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        prof_ev.push_back(e);
+      }
+    }
+    CK(cudaEventRecord(prof_ev[prof_used], stream));
+    return true;
+  }
+  void prof_end(bool on) {
+    if (!on) return;
+    CK(cudaEventRecord(prof_ev[prof_used + 1], stream));
+    prof_used += 2;
+  }
+
+  void release() {
+    for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
+    prof_ev.clear();
+    for (void* p : allocs) cudaFree(p);
+    allocs.clear();
+    if (hbuf) cudaFreeHost(hbuf);
+    hbuf = nullptr;
+    if (own) cudaStreamDestroy(own);
+    own = nullptr;
+  }
+
+  OpL opL() const { return OpL{nullptr, nullptr}; }
+  IpmProblem problem() const {
+    IpmProblem pb;
+    pb.alpha = alpha;
+    pb.beta = beta;
+    pb.dM = mass_diag(g);
+    pb.d = lumped_mass(g);
+    pb.cy = cy;
+    pb.fvec = fvec;
+    pb.L = opL();
+    return pb;
+  }
+  IpmBounds bounds() const { return IpmBounds{ya, yb, zbw, zbv}; }
+  double omega() const { return g.dim == 2 ? 8.0 / 9.0 : 0.95; }
+
+  void sync() {
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(stream));
+  }
+  void fetch(const double* dsrc, int count) {
+    CK(cudaMemcpyAsync(hbuf, dsrc, sizeof(double) * count, cudaMemcpyDeviceToHost, stream));
+    sync();
+  }
+
+  // ------------------------------------------------------------------------
+  template <typename T>
+  void build_mg(MGHier<T>& mg) {
+    int n = g.n;
+    int l = 0;
+    while (true) {
+      MGLevel<T>& L = mg.lv[l];
+      L.g = make_grid(g.dim, n);
+      long long f = L.g.field;
+      L.x[0] = alloc<T>(f);
+      L.x[1] = alloc<T>(f);
+      L.b = alloc<T>(f);
+      L.r = alloc<T>(f);
+      L.jinv = alloc<T>(f);
+      L.m = l == 0 ? nullptr : alloc<T>(f);
+      mg.cur[l] = 0;
+      ++l;
+      if (n == 3) break;
+      n = (n - 1) / 2 + 1;
+    }
+    mg.nlev = l;
+  }
+
+  void create(const ipm_grid* grid, const ipm_pde* p, double a, double b, const ipm_bounds* bd) {
+    if (!grid || !bd) throw IpmError{IPM_EINVAL, "null grid or bounds"};
+    int dim = grid->dim;
+    if (dim != 2 && dim != 3) throw IpmError{IPM_EINVAL, "dim must be 2 or 3"};
+    int n = grid->n[0];
+    for (int k = 1; k < dim; ++k)
+      if (grid->n[k] != n) throw IpmError{IPM_EINVAL, "grids must have equal node counts per direction"};
+    if (n < 3 || ((n - 1) & (n - 2)) != 0)
+      throw IpmError{IPM_EINVAL, "nodes per direction must be 2^k + 1 (k >= 1)"};
+    if (!(a > 0.0) || !(b >= 0.0) || !std::isfinite(a) || !std::isfinite(b))
+      throw IpmError{IPM_EINVAL, "need alpha > 0 and beta >= 0"};
+    pde = p ? *p : ipm_pde{IPM_POISSON, 1.0, 0};
+    if (pde.kind != IPM_POISSON) throw IpmError{IPM_EINVAL, "only the Poisson state equation is built"};
+    g = make_grid(dim, n);
+    alpha = a;
+    beta = b;
+    CK(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+    stream = own;
+    CK(cudaMallocHost(&hbuf, sizeof(double) * 1024));
+    long long f = F();
+    st.y = alloc<double>(f);
+    st.w = alloc<double>(f);
+    st.v = alloc<double>(f);
+    st.p = alloc<double>(f);
+    st.lya = alloc<double>(f);
+    st.lyb = alloc<double>(f);
+    st.lwa = alloc<double>(f);
+    st.lwb = alloc<double>(f);
+    st.lva = alloc<double>(f);
+    st.lvb = alloc<double>(f);
+    ya = alloc<double>(f);
+    yb = alloc<double>(f);
+    zbw = alloc<double>(f);
+    zbv = alloc<double>(f);
+    cy = alloc<double>(f);
+    fvec = alloc<double>(f);
+    glift = alloc<double>(f);
+    dg.thy = alloc<double>(f);
+    dg.thw = alloc<double>(f);
+    dg.thv = alloc<double>(f);
+    dg.mh = alloc<double>(f);
+    dg.thy32 = alloc<float>(f);
+    dg.mh32 = alloc<float>(f);
+    rhs = alloc<double>(4 * f);
+    dx = alloc<double>(4 * f);
+    ktmp = alloc<double>(4 * f);
+    for (int i = 0; i < 3; ++i) cheb64[i] = alloc<double>(f);
+    for (int i = 0; i < 3; ++i) cheb32[i] = alloc<float>(f);
+    build_mg(mg64);
+    build_mg(mg32);
+    part_rows = std::max<long long>(interior_blocks(g), 8 * kRedBlocks);
+    part = alloc<double>(part_rows * 8);
+    dout = alloc<double>(64);
+    sc = alloc<double>(16);
+    kdev = alloc<double>(4 * (kMaxRestart + 2));
+    dense = alloc<double>(nn());
+    set_bounds(bd);
+  }
+
+  // bounds -> fields ya, yb, zbw = max(u_b, 0) = u_b, zbv = -min(u_a, 0) = -u_a
+  void set_bounds(const ipm_bounds* bd) {
+    long long m = nn();
+    std::vector<double> ua(m), ub(m), yav(m), ybv(m);
+    for (long long t = 0; t < m; ++t) {
+      ua[t] = bd->ua_v ? bd->ua_v[t] : bd->ua;
+      ub[t] = bd->ub_v ? bd->ub_v[t] : bd->ub;
+      yav[t] = bd->ya_v ? bd->ya_v[t] : bd->ya;
+      ybv[t] = bd->yb_v ? bd->yb_v[t] : bd->yb;
+    }
+    // validate interior entries
+    int n = g.n;
+    for (long long t = 0; t < m; ++t) {
+      int i = (int)(t % n), j = (int)((t / n) % n), k = g.dim == 3 ? (int)(t / ((long long)n * n)) : 1;
+      bool bnd = i == 0 || j == 0 || i == n - 1 || j == n - 1 || (g.dim == 3 && (k == 0 || k == n - 1));
+      if (bnd) continue;
+      if (!(ua[t] < 0.0) || !(ub[t] > 0.0) || std::isnan(ua[t]) || std::isnan(ub[t]))
+        throw IpmError{IPM_EINVAL, "control bounds must satisfy u_a < 0 < u_b"};
+      if (std::isnan(yav[t]) || std::isnan(ybv[t]) || !(yav[t] < ybv[t]))
+        throw IpmError{IPM_EINVAL, "state bounds must satisfy y_a < y_b"};
+      if (yav[t] == INFINITY || ybv[t] == -INFINITY)
+        throw IpmError{IPM_EINVAL, "state bounds are infeasible"};
+    }
+    for (long long t = 0; t < m; ++t) {
+      ub[t] = std::max(ub[t], 0.0);
+      ua[t] = -std::min(ua[t], 0.0);
+    }
+    upload_field(ybv.data(), yb, 1);
+    upload_field(yav.data(), ya, 1);
+    upload_field(ub.data(), zbw, 1);
+    upload_field(ua.data(), zbv, 1);
+    sync();
+  }
+
+  void upload_field(const double* host, double* field, int mode) {
+    CK(cudaMemcpyAsync(dense, host, sizeof(double) * nn(), cudaMemcpyHostToDevice, stream));
+    launch_pack(g, dense, field, mode, stream);
+  }
+
+  void set_data(const double* yd, const double* f, const double* gb, bool device) {
+    // pack y_d -> rhs[0:F] (scratch), f -> rhs[F:2F], g -> glift (boundary only)
+    double* ydp = rhs;
+    double* fp = rhs + F();
+    auto put = [&](const double* src, double* dst, int mode) {
+      if (!src) {
+        launch_pack(g, nullptr, dst, mode, stream);
+        return;
+      }
+      if (device) {
+        launch_pack(g, src, dst, mode, stream);
+      } else {
+        CK(cudaMemcpyAsync(dense, src, sizeof(double) * nn(), cudaMemcpyHostToDevice, stream));
+        launch_pack(g, dense, dst, mode, stream);
+      }
+    };
+    put(yd, ydp, 0);
+    put(f, fp, 0);
+    put(gb, glift, 2);
+    launch_setup_data(g, ydp, fp, glift, opL(), cy, fvec, stream);
+    launch_element_mass_form(g, ydp, glift, part, dout, stream);
+    launch_setup_norms(g, cy, fvec, bounds(), part, dout + 1, stream);
+    fetch(dout, 4);
+    c0 = hbuf[0];
+    ncy = std::sqrt(hbuf[1]);
+    nf = std::sqrt(hbuf[2]);
+    nbounds = hbuf[3];
+    nd = lumped_mass(g) * std::sqrt((double)nI());
+    has_data = true;
+    solved = false;
+  }
+
+  // ------------------------------------------------------------------------
+  // Multigrid V-cycles on L + diag(m)
+  // ------------------------------------------------------------------------
+  template <typename T>
+  void mg_setup(MGHier<T>& mg, T* m0) {
+    mg.lv[0].m = m0;
+    for (int l = 1; l < mg.nlev; ++l)
+      launch_mg_restrict<T>(mg.lv[l - 1].g, mg.lv[l].g, mg.lv[l - 1].m, mg.lv[l].m, stream);
+    for (int l = 0; l < mg.nlev; ++l)
+      launch_mg_jinv<T>(mg.lv[l].g, opL(), mg.lv[l].m, omega(), mg.lv[l].jinv, stream);
+  }
+
+  template <typename T>
+  void vcycle(MGHier<T>& mg, int l, bool zero_x, int tr, const ipm_options& o) {
+    MGLevel<T>& L = mg.lv[l];
+    int& cur = mg.cur[l];
+    if (l == mg.nlev - 1) {
+      launch_mg_coarsest<T>(L.g, opL(), L.b, L.m, L.x[cur], stream);
+      return;
+    }
+    bool z = zero_x;
+    for (int i = 0; i < o.smooth_pre; ++i) {
+      bool pr = l == 0 && !z && prof_begin();
+      launch_mg_smooth<T>(L.g, opL(), L.x[cur], L.x[1 - cur], L.b, L.m, L.jinv, z, tr, stream);
+      prof_end(pr);
+      cur = 1 - cur;
+      z = false;
+    }
+    if (z) launch_mg_zero<T>(L.g, L.x[cur], stream);
+    launch_mg_residual<T>(L.g, opL(), L.x[cur], L.b, L.m, L.r, tr, stream);
+    MGLevel<T>& C = mg.lv[l + 1];
+    launch_mg_restrict<T>(L.g, C.g, L.r, C.b, stream);
+    vcycle(mg, l + 1, true, tr, o);
+    launch_mg_prolong_add<T>(L.g, C.g, C.x[mg.cur[l + 1]], L.x[cur], stream);
+    for (int i = 0; i < o.smooth_post; ++i) {
+      bool pr = l == 0 && prof_begin();
+      launch_mg_smooth<T>(L.g, opL(), L.x[cur], L.x[1 - cur], L.b, L.m, L.jinv, 0, tr, stream);
+      prof_end(pr);
+      cur = 1 - cur;
+    }
+  }
+
+  // x = (vcycles V-cycles from zero) applied to lv[0].b; returns the level-0 iterate
+  template <typename T>
+  T* mg_solve(MGHier<T>& mg, int tr, const ipm_options& o) {
+    for (int c = 0; c < std::max(1, o.vcycles); ++c) vcycle(mg, 0, c == 0, tr, o);
+    return mg.lv[0].x[mg.cur[0]];
+  }
+
+  // ------------------------------------------------------------------------
+  // Chebyshev semi-iteration for (M + Theta_y) x = r_y (Section 4.1)
+  // ------------------------------------------------------------------------
+  template <typename T, typename To>
+  void cheb_apply(const double* r, const T* thy, To* z, int steps, T* const* buf) {
+    double lmin = g.dim == 2 ? 0.25 : 0.125, lmax = g.dim == 2 ? 2.25 : 3.375;
+    double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sig = theta / delta;
+    T* bT = buf[2];
+    T* cur = buf[0];
+    T* prev = buf[1];
+    double dM = mass_diag(g);
+    launch_cheb_init<T>(g, r, thy, dM, 1.0 / theta, bT, cur, prev, stream);
+    double rho = 1.0 / sig;
+    for (int k = 1; k < steps; ++k) {
+      double rho_new = 1.0 / (2.0 * sig - rho);
+      double om = 2.0 * sig * rho_new;
+      rho = rho_new;
+      if (k == steps - 1) {
+        launch_cheb_step<T, To>(g, cur, prev, bT, thy, dM, om, 1.0 / theta, z, stream);
+        return;
+      }
+      launch_cheb_step<T, T>(g, cur, prev, bT, thy, dM, om, 1.0 / theta, prev, stream);
+      std::swap(cur, prev);
+    }
+    launch_convert<T, To>(g, cur, z, stream);  // steps <= 1
+  }
+
+  // z = P^{-1} r, P = P_T (tri) or P_D (Section 4.2)
+  void precond(const double* r, double* z, int tri, const ipm_options& o) {
+    long long f = F();
+    bool mixed = o.precision == IPM_PREC_MIXED;
+    if (mixed) cheb_apply<float, double>(r, dg.thy32, z, o.cheb_steps, cheb32);
+    else cheb_apply<double, double>(r, dg.thy, z, o.cheb_steps, cheb64);
+    launch_zblock(g, alpha * mass_diag(g), r + f, r + 2 * f, dg.thw, dg.thv, z + f, z + 2 * f,
+                  stream);
+    if (mixed) {
+      launch_coupling<float>(g, opL(), z, z + f, z + 2 * f, r + 3 * f, tri, mg32.lv[0].b, stream);
+      float* s1 = mg_solve(mg32, 0, o);
+      launch_mass_theta<float>(g, s1, dg.thy32, mg32.lv[0].b, stream);
+      float* xp = mg_solve(mg32, 1, o);
+      launch_convert<float, double>(g, xp, z + 3 * f, stream);
+    } else {
+      launch_coupling<double>(g, opL(), z, z + f, z + 2 * f, r + 3 * f, tri, mg64.lv[0].b, stream);
+      double* s1 = mg_solve(mg64, 0, o);
+      launch_mass_theta<double>(g, s1, dg.thy, mg64.lv[0].b, stream);
+      double* xp = mg_solve(mg64, 1, o);
+      launch_convert<double, double>(g, xp, z + 3 * f, stream);
+    }
+  }
+
+  void setup_precond(const ipm_options& o) {
+    if (o.precision == IPM_PREC_MIXED) mg_setup(mg32, dg.mh32);
+    else mg_setup(mg64, dg.mh);
+  }
+
+  void newton_apply(const double* x, double* y) {
+    launch_newton_apply(g, problem(), dg, x, y, stream);
+  }
+
+  double norm(const double* x, long long len) {
+    launch_dot(x, x, len, part, dout, stream);
+    fetch(dout, 1);
+    return std::sqrt(hbuf[0]);
+  }
+
+  void ensure_krylov(const ipm_options& o) {
+    long long f4 = 4 * F();
+    if (o.krylov == IPM_KRYLOV_GMRES_PT) {
+      if (vcap < o.restart) {
+        // buffers only grow; earlier ones stay owned by the arena
+        V = alloc<double>((long long)(o.restart + 1) * f4);
+        Z = alloc<double>((long long)o.restart * f4);
+        vcap = o.restart;
+      }
+    } else if (!mr[0]) {
+      for (int i = 0; i < 14; ++i) mr[i] = alloc<double>(f4);
+    }
+  }
+
+  // ------------------------------------------------------------------------
+  // Right-preconditioned flexible GMRES with classical Gram-Schmidt applied
+  // twice; restarts every o.restart iterations. x0 = 0. The residual estimate
+  // |g_{j+1}| is the unpreconditioned residual norm ||b - A x_j||.
+  // ------------------------------------------------------------------------
+  void fgmres(const ipm_options& o, const double* b, double* x, int tri, int* iters,
+              double* relres) {
+    long long len = 4 * F();
+    long long stride = len;
+    int m = o.restart;
+    double nb = norm(b, len);
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * len, stream));
+    *iters = 0;
+    *relres = 0.0;
+    if (nb == 0.0) return;
+    double tol = o.krylov_tol * nb;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+    int total = 0;
+    bool first = true;
+    double res = nb;
+    while (true) {
+      const double* r0 = b;
+      if (!first) {
+        newton_apply(x, ktmp);
+        launch_axpby(ktmp, b, 1.0, -1.0, len, stream);  // ktmp = b - A x
+        r0 = ktmp;
+        res = norm(ktmp, len);
+        if (res <= tol || total >= o.max_krylov) break;
+      }
+      launch_axpby(V, r0, 1.0 / res, 0.0, len, stream);
+      std::fill(gv.begin(), gv.end(), 0.0);
+      gv[0] = res;
+      int j = 0;
+      bool done = false;
+      for (; j < m && total < o.max_krylov; ++j) {
+        double* vj = V + (long long)j * stride;
+        double* zj = Z + (long long)j * stride;
+        double* w = V + (long long)(j + 1) * stride;
+        precond(vj, zj, tri, o);
+        newton_apply(zj, w);
+        launch_multidot(V, stride, j + 1, w, len, part, kdev, stream);
+        launch_axpy_multi(w, V, stride, j + 1, kdev, -1.0, len, stream);
+        launch_multidot(V, stride, j + 1, w, len, part, kdev + (kMaxRestart + 2), stream);
+        launch_axpy_multi(w, V, stride, j + 1, kdev + (kMaxRestart + 2), -1.0, len, stream);
+        launch_dot(w, w, len, part, kdev + 2 * (kMaxRestart + 2), stream);
+        CK(cudaMemcpyAsync(hbuf, kdev, sizeof(double) * (2 * (kMaxRestart + 2) + 1),
+                           cudaMemcpyDeviceToHost, stream));
+        sync();
+        ++total;
+        double* h = &H[(size_t)j * (m + 1)];
+        for (int i = 0; i <= j; ++i) h[i] = hbuf[i] + hbuf[(kMaxRestart + 2) + i];
+        double hn = std::sqrt(hbuf[2 * (kMaxRestart + 2)]);
+        h[j + 1] = hn;
+        if (!std::isfinite(hn)) throw IpmError{IPM_EBREAKDOWN, "non-finite Krylov vector"};
+        if (hn > 0.0) launch_axpby(w, w, 1.0 / hn, 0.0, len, stream);
+        for (int i = 0; i < j; ++i) {
+          double t = cs[i] * h[i] + sn[i] * h[i + 1];
+          h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+          h[i] = t;
+        }
+        double rr = std::hypot(h[j], h[j + 1]);
+        if (rr == 0.0) throw IpmError{IPM_EBREAKDOWN, "GMRES breakdown (singular Hessenberg)"};
+        cs[j] = h[j] / rr;
+        sn[j] = h[j + 1] / rr;
+        h[j] = rr;
+        h[j + 1] = 0.0;
+        gv[j + 1] = -sn[j] * gv[j];
+        gv[j] = cs[j] * gv[j];
+        res = std::fabs(gv[j + 1]);
+        if (res <= tol || hn == 0.0) {
+          ++j;
+          done = true;
+          break;
+        }
+      }
+      // y = R^{-1} g, x += Z y
+      for (int i = j - 1; i >= 0; --i) {
+        double t = gv[i];
+        for (int k = i + 1; k < j; ++k) t -= H[(size_t)k * (m + 1) + i] * y[k];
+        y[i] = t / H[(size_t)i * (m + 1) + i];
+      }
+      CK(cudaMemcpyAsync(kdev + 3 * (kMaxRestart + 2), y.data(), sizeof(double) * j,
+                         cudaMemcpyHostToDevice, stream));
+      launch_axpy_multi(x, Z, stride, j, kdev + 3 * (kMaxRestart + 2), 1.0, len, stream);
+      sync();  // y lives on the host stack
+      first = false;
+      if (done || total >= o.max_krylov) break;
+    }
+    newton_apply(x, ktmp);
+    launch_axpby(ktmp, b, 1.0, -1.0, len, stream);
+    *relres = norm(ktmp, len) / nb;
+    *iters = total;
+  }
+
+  // ------------------------------------------------------------------------
+  // Preconditioned MINRES (Paige-Saunders) with P = P_D SPD; the unpreconditioned
+  // residual r = b - A x is carried along through A w recurrences.
+  // ------------------------------------------------------------------------
+  double dot(const double* a, const double* b, long long len) {
+    launch_dot(a, b, len, part, dout, stream);
+    fetch(dout, 1);
+    return hbuf[0];
+  }
+
+  void minres(const ipm_options& o, const double* b, double* x, int* iters, double* relres) {
+    long long len = 4 * F();
+    double *v_prev = mr[0], *v_cur = mr[1], *v_next = mr[2], *z_cur = mr[3], *z_next = mr[4];
+    double *w_prev = mr[5], *w_cur = mr[6], *w_next = mr[7], *Az = mr[8];
+    double *aw_prev = mr[9], *aw_cur = mr[10], *aw_next = mr[11], *r = mr[12];
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * len, stream));
+    for (double* p : {v_prev, w_prev, w_cur, aw_prev, aw_cur})
+      CK(cudaMemsetAsync(p, 0, sizeof(double) * len, stream));
+    launch_axpby(r, b, 1.0, 0.0, len, stream);
+    launch_axpby(v_cur, b, 1.0, 0.0, len, stream);
+    *iters = 0;
+    *relres = 0.0;
+    double nb = norm(b, len);
+    if (nb == 0.0) return;
+    precond(v_cur, z_cur, 0, o);
+    double gam = std::sqrt(dot(z_cur, v_cur, len));
+    double gam_prev = 1.0, eta = gam;
+    double s_prev = 0, s_cur = 0, c_prev = 1, c_cur = 1;
+    double tol = o.krylov_tol * nb;
+    double res = nb;
+    int j = 0;
+    while (j < o.max_krylov) {
+      ++j;
+      launch_axpby(z_cur, z_cur, 1.0 / gam, 0.0, len, stream);
+      newton_apply(z_cur, Az);
+      double delta = dot(Az, z_cur, len);
+      launch_lincomb3(v_next, 1.0, Az, -delta / gam, v_cur, -gam / gam_prev, v_prev, len, stream);
+      precond(v_next, z_next, 0, o);
+      double g2 = dot(z_next, v_next, len);
+      if (!(g2 >= 0.0)) throw IpmError{IPM_EBREAKDOWN, "preconditioner not positive definite"};
+      double gam_next = std::sqrt(g2);
+      double a0 = c_cur * delta - c_prev * s_cur * gam;
+      double a1 = std::sqrt(a0 * a0 + gam_next * gam_next);
+      double a2 = s_cur * delta + c_prev * c_cur * gam;
+      double a3 = s_prev * gam;
+      if (a1 == 0.0) throw IpmError{IPM_EBREAKDOWN, "MINRES breakdown"};
+      double c_next = a0 / a1, s_next = gam_next / a1;
+      launch_lincomb3(w_next, 1.0 / a1, z_cur, -a3 / a1, w_prev, -a2 / a1, w_cur, len, stream);
+      launch_lincomb3(aw_next, 1.0 / a1, Az, -a3 / a1, aw_prev, -a2 / a1, aw_cur, len, stream);
+      launch_axpby(x, w_next, c_next * eta, 1.0, len, stream);
+      launch_axpby(r, aw_next, -c_next * eta, 1.0, len, stream);
+      eta = -s_next * eta;
+      res = norm(r, len);
+      std::swap(v_prev, v_cur);
+      std::swap(v_cur, v_next);
+      std::swap(z_cur, z_next);
+      gam_prev = gam;
+      gam = gam_next;
+      std::swap(w_prev, w_cur);
+      std::swap(w_cur, w_next);
+      std::swap(aw_prev, aw_cur);
+      std::swap(aw_cur, aw_next);
+      c_prev = c_cur;
+      c_cur = c_next;
+      s_prev = s_cur;
+      s_cur = s_next;
+      if (!std::isfinite(res)) throw IpmError{IPM_EBREAKDOWN, "non-finite MINRES residual"};
+      if (res <= tol || gam == 0.0) break;
+    }
+    newton_apply(x, ktmp);
+    launch_axpby(ktmp, b, 1.0, -1.0, len, stream);
+    *relres = norm(ktmp, len) / nb;
+    *iters = j;
+  }
+
+  void krylov(const ipm_options& o, const double* b, double* x, int* iters, double* relres) {
+    if (o.krylov == IPM_KRYLOV_GMRES_PT) fgmres(o, b, x, 1, iters, relres);
+    else minres(o, b, x, iters, relres);
+  }
+
+  // ------------------------------------------------------------------------
+  // Algorithm A.1
+  // ------------------------------------------------------------------------
+  void residual_row(double mu, int k, double aP, double aD, int kit, double krr) {
+    launch_residuals(g, problem(), bounds(), st, mu, part, dout, stream);
+    fetch(dout, 8);
+    double* q = hbuf;
+    double xp = std::sqrt(q[0]), xd = std::sqrt(q[1]), xc = std::sqrt(q[2]);
+    double Q = 0.5 * (q[4] - 2.0 * q[5] + c0) + 0.5 * alpha * q[6] + beta * lumped_mass(g) * q[7];
+    double rp = xp / (1.0 + nf + ncy);
+    double rd = xd / (1.0 + ncy + beta * nd);
+    double rc = nbounds > 0 ? (q[3] / nbounds) / (1.0 + std::fabs(Q)) : 0.0;
+    double kkt = std::max(rp, std::max(rd, rc));
+    double row[kHistCols] = {(double)k, mu, xp, xd, xc, kkt, aP, aD, (double)kit, krr};
+    hist.insert(hist.end(), row, row + kHistCols);
+  }
+
+  int solve(const ipm_options& o, ipm_report* rep) {
+    if (!has_data) throw IpmError{IPM_ESTATE, "ipm_set_data must precede ipm_solve"};
+    if (o.restart < 1 || o.restart > kMaxRestart) throw IpmError{IPM_EINVAL, "restart out of range [1, 100]"};
+    if (o.cheb_steps < 1 || o.vcycles < 1 || o.smooth_pre < 0 || o.smooth_post < 0 ||
+        !(o.sigma > 0 && o.sigma < 1) || !(o.alpha0 > 0 && o.alpha0 < 1) || !(o.mu0 > 0) ||
+        o.max_krylov < 1 || o.max_ipm < 0)
+      throw IpmError{IPM_EINVAL, "invalid solver options"};
+    if (o.smooth_pre != o.smooth_post && o.krylov == IPM_KRYLOV_MINRES_PD)
+      throw IpmError{IPM_EINVAL, "MINRES needs a symmetric V-cycle (smooth_pre == smooth_post)"};
+    auto t0 = std::chrono::steady_clock::now();
+    ensure_krylov(o);
+    hist.clear();
+    double mu = o.mu0;
+    launch_init_state(g, bounds(), st, mu, stream);
+    residual_row(mu, 0, 0.0, 0.0, 0, 0.0);
+    int k = 0, status = IPM_OK, ktot = 0;
+    double krr_max = 0.0;
+    while (true) {
+      const double* h = &hist[hist.size() - kHistCols];
+      bool stop;
+      if (o.stop == IPM_STOP_FIXED) stop = k >= o.fixed_iters;
+      else if (o.stop == IPM_STOP_PAPER) stop = h[2] <= o.eps_p && h[3] <= o.eps_d && h[4] <= o.eps_c;
+      else stop = h[5] <= o.kkt_tol;
+      if (stop) break;
+      if (k >= o.max_ipm) {
+        status = IPM_ENOTCONV;
+        break;
+      }
+      double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (o.time_limit_s > 0 && el > o.time_limit_s) {
+        status = IPM_ETIMEOUT;
+        break;
+      }
+      mu *= o.sigma;
+      launch_prep(g, problem(), bounds(), st, dg, mu, rhs, o.precision == IPM_PREC_MIXED, stream);
+      setup_precond(o);
+      int kit = 0;
+      double krr = 0.0;
+      krylov(o, rhs, dx, &kit, &krr);
+      ktot += kit;
+      krr_max = std::max(krr_max, krr);
+      launch_steplen(g, bounds(), st, dx, mu, o.alpha0, part, sc, stream);
+      launch_update(g, bounds(), st, dx, mu, sc, stream);
+      ++k;
+      fetch(sc, 2);
+      double aP = hbuf[0], aD = hbuf[1];
+      residual_row(mu, k, aP, aD, kit, krr);
+      if (!std::isfinite(hist[hist.size() - kHistCols + 5]))
+        throw IpmError{IPM_EBREAKDOWN, "non-finite residuals"};
+    }
+    solved = true;
+    if (rep) {
+      const double* h = &hist[hist.size() - kHistCols];
+      rep->status = status;
+      rep->ipm_iters = k;
+      rep->krylov_iters_total = ktot;
+      rep->kkt_rel = h[5];
+      rep->xi_p = h[2];
+      rep->xi_d = h[3];
+      rep->xi_c = h[4];
+      rep->mu = mu;
+      rep->krylov_relres_max = krr_max;
+      rep->seconds =
+          std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return status;
+  }
+
+  void get(int which, double* out, size_t len, bool device) const {
+    if (!solved) throw IpmError{IPM_ESTATE, "no solution yet"};
+    if ((long long)len != nn()) throw IpmError{IPM_EINVAL, "output length must be n^d"};
+    ipm_solver* self = const_cast<ipm_solver*>(this);
+    const double* src = which == 0 ? st.y : which == 2 ? st.p : nullptr;
+    double* tgt = device ? out : self->dense;
+    if (which == 1) {
+      // u = w - v into the dense scratch through ktmp
+      launch_lincomb3(self->ktmp, 1.0, st.w, -1.0, st.v, 0.0, nullptr, F(), stream);
+      src = self->ktmp;
+    }
+    launch_unpack(g, src, which == 0 ? glift : nullptr, tgt, stream);
+    if (!device)
+      CK(cudaMemcpyAsync(out, self->dense, sizeof(double) * nn(), cudaMemcpyDeviceToHost, stream));
+    self->sync();
+  }
+};
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+namespace {
+template <typename Fn>
+int guarded(ipm_solver* s, Fn fn) {
+  try {
+    return fn();
+  } catch (const IpmError& e) {
+    if (s) s->err = e.msg;
+    return e.code;
+  } catch (const std::exception& e) {
+    if (s) s->err = e.what();
+    return IPM_ECUDA;
+  }
+}
+thread_local std::string g_create_err;
+}  // namespace
+
+extern "C" {
+
+void ipm_default_options(ipm_options* o) {
+  if (!o) return;
+  o->precision = IPM_PREC_FP64;
+  o->krylov = IPM_KRYLOV_GMRES_PT;
+  o->stop = IPM_STOP_PAPER;
+  o->sigma = 0.2;
+  o->alpha0 = 0.995;
+  o->eps_p = o->eps_d = o->eps_c = 1e-6;
+  o->mu0 = 1.0;
+  o->kkt_tol = 1e-6;
+  o->krylov_tol = 1e-10;
+  o->cheb_steps = 20;
+  o->vcycles = 3;
+  o->smooth_pre = 5;
+  o->smooth_post = 5;
+  o->max_ipm = 100;
+  o->max_krylov = 200;
+  o->restart = 50;
+  o->fixed_iters = 0;
+  o->time_limit_s = 0.0;
+}
+
+int ipm_create(const ipm_grid* grid, const ipm_pde* pde, double alpha, double beta,
+               const ipm_bounds* bounds, ipm_solver** out) {
+  if (!out) return IPM_EINVAL;
+  *out = nullptr;
+  ipm_solver* s = new ipm_solver();
+  int rc = guarded(s, [&] {
+    s->create(grid, pde, alpha, beta, bounds);
+    return IPM_OK;
+  });
+  if (rc != IPM_OK) {
+    g_create_err = s->err;
+    s->release();
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return IPM_OK;
+}
+
+int ipm_set_stream(ipm_solver* s, void* stream) {
+  if (!s) return IPM_EINVAL;
+  s->stream = stream ? (cudaStream_t)stream : s->own;
+  return IPM_OK;
+}
+
+int ipm_set_data(ipm_solver* s, const double* yd, const double* f, const double* g) {
+  if (!s) return IPM_EINVAL;
+  return guarded(s, [&] {
+    s->set_data(yd, f, g, false);
+    return IPM_OK;
+  });
+}
+
+int ipm_set_data_device(ipm_solver* s, const double* yd, const double* f, const double* g) {
+  if (!s) return IPM_EINVAL;
+  return guarded(s, [&] {
+    s->set_data(yd, f, g, true);
+    return IPM_OK;
+  });
+}
+
+int ipm_solve(ipm_solver* s, const ipm_options* opt, ipm_report* rep) {
+  if (!s) return IPM_EINVAL;
+  ipm_options o;
+  if (opt) o = *opt;
+  else ipm_default_options(&o);
+  return guarded(s, [&] { return s->solve(o, rep); });
+}
+
+static int get_common(const ipm_solver* s, int which, double* out, size_t len, bool dev) {
+  if (!s || !out) return IPM_EINVAL;
+  ipm_solver* m = const_cast<ipm_solver*>(s);
+  return guarded(m, [&] {
+    s->get(which, out, len, dev);
+    return IPM_OK;
+  });
+}
+int ipm_get_state(const ipm_solver* s, double* y, size_t len) { return get_common(s, 0, y, len, false); }
+int ipm_get_control(const ipm_solver* s, double* u, size_t len) { return get_common(s, 1, u, len, false); }
+int ipm_get_adjoint(const ipm_solver* s, double* p, size_t len) { return get_common(s, 2, p, len, false); }
+int ipm_get_state_device(const ipm_solver* s, double* y, size_t len) { return get_common(s, 0, y, len, true); }
+int ipm_get_control_device(const ipm_solver* s, double* u, size_t len) { return get_common(s, 1, u, len, true); }
+int ipm_get_adjoint_device(const ipm_solver* s, double* p, size_t len) { return get_common(s, 2, p, len, true); }
+
+int ipm_get_history(const ipm_solver* s, double* rows, int max_rows, int* n_rows) {
+  if (!s || !n_rows) return IPM_EINVAL;
+  int nr = (int)(s->hist.size() / kHistCols);
+  *n_rows = nr;
+  if (rows && max_rows > 0)
+    std::memcpy(rows, s->hist.data(), sizeof(double) * kHistCols * std::min(nr, max_rows));
+  return IPM_OK;
+}
+
+void ipm_destroy(ipm_solver* s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  s->release();
+  delete s;
+}
+
+const char* ipm_strerror(int code) {
+  switch (code) {
+    case IPM_OK: return "ok";
+    case IPM_EINVAL: return "invalid argument";
+    case IPM_ENOMEM: return "out of device memory";
+    case IPM_ENOTCONV: return "iteration limit reached before convergence";
+    case IPM_EBREAKDOWN: return "Krylov breakdown or non-finite values";
+    case IPM_ETIMEOUT: return "time limit reached";
+    case IPM_ECUDA: return "CUDA error";
+    case IPM_ESTATE: return "call out of order";
+    default: return "unknown error";
+  }
+}
+
+long long ipm_launch_count(void) { return launches_total(); }
+
+int ipm_profile_smoother(ipm_solver* s, int enable, int every) {
+  if (!s || every < 1) return IPM_EINVAL;
+  return guarded(s, [&] {
+    s->prof_flush();
+    s->prof_on = enable != 0;
+    s->prof_every = every;
+    s->prof_seen = 0;
+    s->prof_ms = 0.0;
+    s->prof_count = 0;
+    return IPM_OK;
+  });
+}
+
+int ipm_profile_read(ipm_solver* s, double* total_ms, long long* launches, double* bytes_per_launch) {
+  if (!s) return IPM_EINVAL;
+  return guarded(s, [&] {
+    s->prof_flush();
+    if (total_ms) *total_ms = s->prof_ms;
+    if (launches) *launches = s->prof_count;
+    // algorithmic bytes of one finest-level Jacobi sweep: read x, b, m, jinv; write x
+    long long m = s->g.n - 2;
+    long long unknowns = s->g.dim == 3 ? m * m * m : m * m;
+    if (bytes_per_launch) *bytes_per_launch = 5.0 * (double)unknowns * 4.0;
+    return IPM_OK;
+  });
+}
+
+const char* ipm_last_error(const ipm_solver* s) {
+  return s ? s->err.c_str() : g_create_err.c_str();
+}
+
+// ---------------------------------------------------------------------------
+// Component entry points
+// ---------------------------------------------------------------------------
+int ipm_newton_apply_device(ipm_solver* s, const double* ty, const double* tw, const double* tv,
+                            const double* x, double* out) {
+  if (!s || !ty || !tw || !tv || !x || !out) return IPM_EINVAL;
+  return guarded(s, [&] {
+    long long f = s->F(), m = s->nn();
+    launch_pack(s->g, ty, s->dg.thy, 1, s->stream);
+    launch_pack(s->g, tw, s->dg.thw, 1, s->stream);
+    launch_pack(s->g, tv, s->dg.thv, 1, s->stream);
+    for (int b = 0; b < 4; ++b) launch_pack(s->g, x + b * m, s->rhs + b * f, 1, s->stream);
+    s->newton_apply(s->rhs, s->dx);
+    for (int b = 0; b < 4; ++b) launch_unpack(s->g, s->dx + b * f, nullptr, out + b * m, s->stream);
+    s->sync();
+    return IPM_OK;
+  });
+}
+
+static void load_diags(ipm_solver* s, const double* ty, const double* tw, const double* tv) {
+  launch_pack(s->g, ty, s->dg.thy, 1, s->stream);
+  launch_pack(s->g, tw, s->dg.thw, 1, s->stream);
+  launch_pack(s->g, tv, s->dg.thv, 1, s->stream);
+  launch_mhat(s->g, s->alpha, mass_diag(s->g), s->dg.thy, s->dg.thw, s->dg.thv, s->dg.mh,
+              s->dg.thy32, s->dg.mh32, s->stream);
+}
+
+int ipm_precond_apply_device(ipm_solver* s, const ipm_options* opt, int tri, const double* ty,
+                             const double* tw, const double* tv, const double* r, double* z) {
+  if (!s || !ty || !tw || !tv || !r || !z) return IPM_EINVAL;
+  ipm_options o;
+  if (opt) o = *opt;
+  else ipm_default_options(&o);
+  return guarded(s, [&] {
+    long long f = s->F(), m = s->nn();
+    load_diags(s, ty, tw, tv);
+    s->setup_precond(o);
+    for (int b = 0; b < 4; ++b) launch_pack(s->g, r + b * m, s->rhs + b * f, 1, s->stream);
+    s->precond(s->rhs, s->dx, tri, o);
+    for (int b = 0; b < 4; ++b) launch_unpack(s->g, s->dx + b * f, nullptr, z + b * m, s->stream);
+    s->sync();
+    return IPM_OK;
+  });
+}
+
+int ipm_chebyshev_device(ipm_solver* s, int steps, const double* ty, const double* b, double* x) {
+  if (!s || !ty || !b || !x || steps < 1) return IPM_EINVAL;
+  return guarded(s, [&] {
+    launch_pack(s->g, ty, s->dg.thy, 1, s->stream);
+    launch_pack(s->g, b, s->rhs, 1, s->stream);
+    s->cheb_apply<double, double>(s->rhs, s->dg.thy, s->dx, steps, s->cheb64);
+    launch_unpack(s->g, s->dx, nullptr, x, s->stream);
+    s->sync();
+    return IPM_OK;
+  });
+}
+
+int ipm_vcycle_device(ipm_solver* s, const ipm_options* opt, int tr, const double* m,
+                      const double* b, double* x) {
+  if (!s || !m || !b || !x) return IPM_EINVAL;
+  ipm_options o;
+  if (opt) o = *opt;
+  else ipm_default_options(&o);
+  return guarded(s, [&] {
+    launch_pack(s->g, m, s->dg.mh, 1, s->stream);
+    s->mg_setup(s->mg64, s->dg.mh);
+    launch_pack(s->g, b, s->mg64.lv[0].b, 1, s->stream);
+    double* xr = s->mg_solve(s->mg64, tr, o);
+    launch_unpack(s->g, xr, nullptr, x, s->stream);
+    s->sync();
+    return IPM_OK;
+  });
+}
+
+int ipm_newton_step_device(ipm_solver* s, const ipm_options* opt, const double* const* it,
+                           double mu, double* dxo, int* iters, double* relres) {
+  if (!s || !it || !dxo) return IPM_EINVAL;
+  ipm_options o;
+  if (opt) o = *opt;
+  else ipm_default_options(&o);
+  return guarded(s, [&] {
+    if (!s->has_data) throw IpmError{IPM_ESTATE, "ipm_set_data must come first"};
+    double* dst[10] = {s->st.y, s->st.w, s->st.v, s->st.p, s->st.lya,
+                       s->st.lyb, s->st.lwa, s->st.lwb, s->st.lva, s->st.lvb};
+    for (int q = 0; q < 10; ++q) launch_pack(s->g, it[q], dst[q], 1, s->stream);
+    s->ensure_krylov(o);
+    launch_prep(s->g, s->problem(), s->bounds(), s->st, s->dg, mu, s->rhs,
+                o.precision == IPM_PREC_MIXED, s->stream);
+    s->setup_precond(o);
+    int kit = 0;
+    double krr = 0;
+    s->krylov(o, s->rhs, s->dx, &kit, &krr);
+    long long f = s->F(), m = s->nn();
+    for (int b = 0; b < 4; ++b) launch_unpack(s->g, s->dx + b * f, nullptr, dxo + b * m, s->stream);
+    s->sync();
+    if (iters) *iters = kit;
+    if (relres) *relres = krr;
+    return IPM_OK;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,296 @@
+"""Python binding of libipm (include/ipm.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module converts numpy
+arrays / torch CUDA tensors to pointers and C structs. Importing it never
+falls back to anything else: if ``libipm.so`` is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libipm.so")
+_lib = None
+
+OK, EINVAL, ENOMEM, ENOTCONV, EBREAKDOWN, ETIMEOUT, ECUDA, ESTATE = range(8)
+PREC_FP64, PREC_MIXED = 0, 1
+KRYLOV_MINRES_PD, KRYLOV_GMRES_PT = 0, 1
+STOP_PAPER, STOP_KKT, STOP_FIXED = 0, 1, 2
+POISSON, CONVDIFF_SUPG = 0, 1
+
+HIST_COLS = ("k", "mu", "xi_p", "xi_d", "xi_c", "kkt_rel", "alpha_P", "alpha_D",
+             "krylov_iters", "krylov_relres")
+
+EXPORTED = (
+    "ipm_default_options", "ipm_create", "ipm_set_stream", "ipm_set_data",
+    "ipm_set_data_device", "ipm_solve", "ipm_get_state", "ipm_get_control", "ipm_get_adjoint",
+    "ipm_get_state_device", "ipm_get_control_device", "ipm_get_adjoint_device",
+    "ipm_get_history", "ipm_destroy", "ipm_launch_count",
+    "ipm_profile_smoother", "ipm_profile_read", "ipm_strerror", "ipm_last_error",
+    "ipm_newton_apply_device", "ipm_precond_apply_device", "ipm_chebyshev_device",
+    "ipm_vcycle_device", "ipm_newton_step_device",
+)
+
+
+class Grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3)]
+
+
+class Pde(C.Structure):
+    _fields_ = [("kind", C.c_int), ("eps", C.c_double), ("wind", C.c_int)]
+
+
+class Bounds(C.Structure):
+    _fields_ = [("ua", C.c_double), ("ub", C.c_double), ("ya", C.c_double), ("yb", C.c_double),
+                ("ua_v", C.POINTER(C.c_double)), ("ub_v", C.POINTER(C.c_double)),
+                ("ya_v", C.POINTER(C.c_double)), ("yb_v", C.POINTER(C.c_double))]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("krylov", C.c_int), ("stop", C.c_int),
+                ("sigma", C.c_double), ("alpha0", C.c_double), ("eps_p", C.c_double),
+                ("eps_d", C.c_double), ("eps_c", C.c_double), ("mu0", C.c_double),
+                ("kkt_tol", C.c_double), ("krylov_tol", C.c_double),
+                ("cheb_steps", C.c_int), ("vcycles", C.c_int), ("smooth_pre", C.c_int),
+                ("smooth_post", C.c_int), ("max_ipm", C.c_int), ("max_krylov", C.c_int),
+                ("restart", C.c_int), ("fixed_iters", C.c_int), ("time_limit_s", C.c_double)]
+
+
+class Report(C.Structure):
+    _fields_ = [("status", C.c_int), ("ipm_iters", C.c_int), ("krylov_iters_total", C.c_int),
+                ("kkt_rel", C.c_double), ("xi_p", C.c_double), ("xi_d", C.c_double),
+                ("xi_c", C.c_double), ("mu", C.c_double), ("krylov_relres_max", C.c_double),
+                ("seconds", C.c_double)]
+
+
+class IpmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libipm error {code}: {msg}")
+        self.code = code
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load() -> C.CDLL:
+    """Load libipm.so (built by ``paper_1806_05896_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libipm.so not built ({_LIB_PATH}); run __graft_entry__.build()")
+    lib = C.CDLL(_LIB_PATH)
+    P = C.c_void_p
+    D = C.POINTER(C.c_double)
+    lib.ipm_default_options.argtypes = [C.POINTER(Options)]
+    lib.ipm_default_options.restype = None
+    lib.ipm_create.argtypes = [C.POINTER(Grid), C.POINTER(Pde), C.c_double, C.c_double,
+                               C.POINTER(Bounds), C.POINTER(P)]
+    lib.ipm_set_stream.argtypes = [P, P]
+    lib.ipm_set_data.argtypes = [P, D, D, D]
+    lib.ipm_set_data_device.argtypes = [P, P, P, P]
+    lib.ipm_solve.argtypes = [P, C.POINTER(Options), C.POINTER(Report)]
+    for nm in ("ipm_get_state", "ipm_get_control", "ipm_get_adjoint"):
+        getattr(lib, nm).argtypes = [P, D, C.c_size_t]
+        getattr(lib, nm + "_device").argtypes = [P, P, C.c_size_t]
+    lib.ipm_get_history.argtypes = [P, D, C.c_int, C.POINTER(C.c_int)]
+    lib.ipm_destroy.argtypes = [P]
+    lib.ipm_destroy.restype = None
+    lib.ipm_launch_count.argtypes = []
+    lib.ipm_launch_count.restype = C.c_longlong
+    lib.ipm_profile_smoother.argtypes = [P, C.c_int, C.c_int]
+    lib.ipm_profile_read.argtypes = [P, D, C.POINTER(C.c_longlong), D]
+    lib.ipm_strerror.argtypes = [C.c_int]
+    lib.ipm_strerror.restype = C.c_char_p
+    lib.ipm_last_error.argtypes = [P]
+    lib.ipm_last_error.restype = C.c_char_p
+    lib.ipm_newton_apply_device.argtypes = [P, P, P, P, P, P]
+    lib.ipm_precond_apply_device.argtypes = [P, C.POINTER(Options), C.c_int, P, P, P, P, P]
+    lib.ipm_chebyshev_device.argtypes = [P, C.c_int, P, P, P]
+    lib.ipm_vcycle_device.argtypes = [P, C.POINTER(Options), C.c_int, P, P, P]
+    lib.ipm_newton_step_device.argtypes = [P, C.POINTER(Options), C.POINTER(P), C.c_double, P,
+                                           C.POINTER(C.c_int), D]
+    _lib = lib
+    return lib
+
+
+def launch_count() -> int:
+    """Kernel launches enqueued by libipm so far (this process)."""
+    return int(load().ipm_launch_count())
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().ipm_default_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _dptr(a) -> int:
+    """Device pointer of a contiguous torch CUDA float64 tensor."""
+    if a is None:
+        return None
+    if not (a.is_cuda and a.dtype.is_floating_point and a.element_size() == 8 and a.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return a.data_ptr()
+
+
+def _hptr(a):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Solver:
+    """One problem instance on the current CUDA device (owns its device memory)."""
+
+    def __init__(self, dim: int, n: int, alpha: float, beta: float, ua, ub,
+                 ya=-math.inf, yb=math.inf, kind: str = "poisson", eps: float = 1.0):
+        lib = load()
+        self._lib = lib
+        self.dim, self.n = dim, n
+        g = Grid(dim, (C.c_int * 3)(n, n, n if dim == 3 else 0))
+        pde = Pde(POISSON if kind == "poisson" else CONVDIFF_SUPG, eps, 0)
+        keep = []
+
+        def bnd(v):
+            a = np.asarray(v, dtype=np.float64)
+            if a.ndim == 0:
+                return float(a), None
+            a = np.ascontiguousarray(a.reshape(-1))
+            keep.append(a)
+            return 0.0, a.ctypes.data_as(C.POINTER(C.c_double))
+        (sua, pua), (sub, pub), (sya, pya), (syb, pyb) = bnd(ua), bnd(ub), bnd(ya), bnd(yb)
+        b = Bounds(sua, sub, sya, syb, pua, pub, pya, pyb)
+        h = C.c_void_p()
+        rc = lib.ipm_create(C.byref(g), C.byref(pde), alpha, beta, C.byref(b), C.byref(h))
+        if rc != OK:
+            raise IpmError(rc, lib.ipm_last_error(None).decode())
+        self._h = h
+
+    # ------------------------------------------------------------------
+    def _check(self, rc: int, ok=(OK,)):
+        if rc not in ok:
+            raise IpmError(rc, self._lib.ipm_last_error(self._h).decode())
+        return rc
+
+    @property
+    def nodes(self) -> int:
+        return self.n ** self.dim
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ipm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream_handle: Optional[int]):
+        self._check(self._lib.ipm_set_stream(self._h, stream_handle))
+
+    def set_data(self, yd=None, f=None, g=None):
+        """Host nodal arrays (n^d, C order, x fastest); None = zero."""
+        args = [_hptr(a) for a in (yd, f, g)]
+        self._check(self._lib.ipm_set_data(self._h, *[a[1] if a else None for a in args]))
+
+    def set_data_device(self, yd=None, f=None, g=None):
+        """Torch CUDA float64 tensors of n^d entries; None = zero."""
+        self._check(self._lib.ipm_set_data_device(self._h, _dptr(yd), _dptr(f), _dptr(g)))
+
+    def solve(self, options: Optional[Options] = None, **kw) -> dict:
+        o = options if options is not None else default_options(**kw)
+        r = Report()
+        self._check(self._lib.ipm_solve(self._h, C.byref(o), C.byref(r)), ok=(OK, ENOTCONV))
+        return {f: getattr(r, f) for f, _ in Report._fields_}
+
+    def _get(self, name: str):
+        out = np.empty(self.nodes)
+        self._check(getattr(self._lib, name)(self._h, out.ctypes.data_as(C.POINTER(C.c_double)),
+                                             out.size))
+        return out.reshape((self.n,) * self.dim)
+
+    def state(self):
+        return self._get("ipm_get_state")
+
+    def control(self):
+        return self._get("ipm_get_control")
+
+    def adjoint(self):
+        return self._get("ipm_get_adjoint")
+
+    def get_device(self, which: str, out):
+        nm = {"state": "ipm_get_state_device", "control": "ipm_get_control_device",
+              "adjoint": "ipm_get_adjoint_device"}[which]
+        self._check(getattr(self._lib, nm)(self._h, _dptr(out), out.numel()))
+        return out
+
+    def profile_smoother(self, enable: bool, every: int = 8):
+        self._check(self._lib.ipm_profile_smoother(self._h, int(enable), every))
+
+    def profile_read(self):
+        ms = C.c_double()
+        cnt = C.c_longlong()
+        by = C.c_double()
+        self._check(self._lib.ipm_profile_read(self._h, C.byref(ms), C.byref(cnt), C.byref(by)))
+        return ms.value, cnt.value, by.value
+
+    def history(self) -> list:
+        nr = C.c_int()
+        self._check(self._lib.ipm_get_history(self._h, None, 0, C.byref(nr)))
+        buf = np.zeros((max(nr.value, 1), len(HIST_COLS)))
+        self._check(self._lib.ipm_get_history(self._h, buf.ctypes.data_as(C.POINTER(C.c_double)),
+                                              nr.value, C.byref(nr)))
+        return [dict(zip(HIST_COLS, row)) for row in buf[:nr.value]]
+
+    # ------------------------------------------------------------------
+    # component entry points (torch CUDA float64 tensors)
+    # ------------------------------------------------------------------
+    def newton_apply(self, th_y, th_w, th_v, x, out):
+        self._check(self._lib.ipm_newton_apply_device(self._h, _dptr(th_y), _dptr(th_w),
+                                                      _dptr(th_v), _dptr(x), _dptr(out)))
+        return out
+
+    def precond_apply(self, triangular: bool, th_y, th_w, th_v, r, z, options=None, **kw):
+        o = options if options is not None else default_options(**kw)
+        self._check(self._lib.ipm_precond_apply_device(self._h, C.byref(o), int(triangular),
+                                                       _dptr(th_y), _dptr(th_w), _dptr(th_v),
+                                                       _dptr(r), _dptr(z)))
+        return z
+
+    def chebyshev(self, steps: int, th_y, b, x):
+        self._check(self._lib.ipm_chebyshev_device(self._h, steps, _dptr(th_y), _dptr(b), _dptr(x)))
+        return x
+
+    def vcycle(self, transpose: bool, m, b, x, options=None, **kw):
+        o = options if options is not None else default_options(**kw)
+        self._check(self._lib.ipm_vcycle_device(self._h, C.byref(o), int(transpose), _dptr(m),
+                                                _dptr(b), _dptr(x)))
+        return x
+
+    def newton_step(self, iterate: Sequence, mu: float, dx, options=None, **kw):
+        o = options if options is not None else default_options(**kw)
+        arr = (C.c_void_p * 10)(*[_dptr(a) for a in iterate])
+        it = C.c_int()
+        rr = C.c_double()
+        self._check(self._lib.ipm_newton_step_device(self._h, C.byref(o), arr, mu, _dptr(dx),
+                                                     C.byref(it), C.byref(rr)))
+        return it.value, rr.value

@@ -1,0 +1,61 @@
+"""The C-ABI library builds, loads, and exports every function include/ipm.h declares (no GPU)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1806_05896_gb300 import build, ipm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "ipm.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ipm_[a-z_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return ipm.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 20
+    out = subprocess.run(["nm", "-D", "--defined-only", ipm.lib_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r" T (ipm_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    assert set(ipm.EXPORTED) == set(names)
+    for n in names:
+        assert hasattr(lib, n)
+
+
+def test_default_options_are_the_papers(lib):
+    o = ipm.default_options()
+    assert (o.sigma, o.alpha0, o.eps_p, o.eps_d, o.eps_c) == (0.2, 0.995, 1e-6, 1e-6, 1e-6)
+    assert (o.krylov_tol, o.cheb_steps, o.vcycles, o.smooth_pre, o.smooth_post) == (1e-10, 20, 3, 5, 5)
+    assert o.mu0 == 1.0
+
+
+def test_strerror_without_gpu(lib):
+    assert lib.ipm_strerror(ipm.EINVAL).decode() == "invalid argument"
+    assert lib.ipm_strerror(99).decode() == "unknown error"
+
+
+def test_library_is_built_for_sm103a(lib):
+    """The fatbinary carries sm_103a code (checked from the build flags, not by disassembly)."""
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1806_05896_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "from oracle" not in src and "import oracle" not in src

@@ -1,0 +1,163 @@
+"""Whole interior point solves on the GPU vs the oracle (Algorithm A.1 with direct Newton solves).
+
+Both sides run the same number of IPM iterations (same mu^k) from the same start and are
+compared at their final iterates. Bars: relative L2 error <= 1e-8 on u, y, p for the FP64 path
+(alpha >= 1e-4) and <= 1e-6 for the mixed path.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import ipm as oipm
+from oracle import qp as Q
+from paper_1806_05896_gb300 import ipm
+
+from gpu_util import dev, host, rel, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_pair(wl, k, **opts):
+    qp = Q.from_workload(wl)
+    ref = oipm.solve(qp, sigma=wl.sigma, n_iter=k)
+    s = ipm.Solver(wl.dim, wl.n, wl.alpha, wl.beta, wl.ua, wl.ub, wl.ya, wl.yb)
+    s.set_data(wl.yd)
+    rep = s.solve(stop=ipm.STOP_FIXED, fixed_iters=k, sigma=wl.sigma, **opts)
+    got = dict(y=s.state().reshape(-1), u=s.control().reshape(-1), p=s.adjoint().reshape(-1))
+    want = dict(y=ref.y_full(qp), u=qp.full(ref.u()), p=qp.full(ref.state.p))
+    hist = s.history()
+    s.close()
+    return got, want, rep, hist, ref
+
+
+def _iters_to(wl, tol):
+    qp = Q.from_workload(wl)
+    r = oipm.solve(qp, sigma=wl.sigma, stop="kkt", kkt_tol=tol)
+    return len(r.history) - 1
+
+
+@pytest.mark.parametrize("krylov", [ipm.KRYLOV_MINRES_PD, ipm.KRYLOV_GMRES_PT])
+def test_poisson_33_fp64(krylov):
+    """The 33^2 Poisson configuration (alpha 1e-2, beta 1e-3, u in [-2, 2]) driven to kkt_rel 1e-10."""
+    wl = W.workload_c1()
+    k = _iters_to(wl, 1e-10)
+    got, want, rep, hist, ref = _run_pair(wl, k, krylov=krylov)
+    for f in ("y", "u", "p"):
+        assert rel(got[f], want[f]) < 1e-8, (f, rel(got[f], want[f]))
+    assert rep["ipm_iters"] == k and rep["krylov_relres_max"] < 1.5e-10
+    for a, b in zip(hist, ref.history):
+        assert a["mu"] == b["mu"]
+        assert abs(a["kkt_rel"] - b["kkt_rel"]) <= 1e-6 * b["kkt_rel"] + 1e-14
+        if a["k"] > 0:
+            assert abs(a["alpha_P"] - b["alpha_P"]) < 1e-8 and abs(a["alpha_D"] - b["alpha_D"]) < 1e-8
+
+
+@pytest.mark.parametrize("cell", [0, 1, 2, 3, 4, 5])
+def test_gaussian_state_bound_65(cell):
+    """y <= 0.1, Gaussian-sum y_d, u in [-30, 30] (the 1025^2 sweep's recipe at 65^2), alpha >= 1e-4."""
+    wl = W.workload_c2(n=65, cell=cell)
+    k = _iters_to(wl, 1e-10)
+    got, want, rep, _, _ = _run_pair(wl, k)
+    for f in ("y", "u", "p"):
+        assert rel(got[f], want[f]) < 1e-8, (f, rel(got[f], want[f]))
+    assert got["y"].max() <= 0.1
+
+
+@pytest.mark.parametrize("cell", [1, 4, 7])
+def test_mixed_precision_gaussian_65(cell):
+    wl = W.workload_c2(n=65, cell=cell)
+    k = _iters_to(wl, 1e-6)
+    got, want, rep, _, _ = _run_pair(wl, k, precision=ipm.PREC_MIXED)
+    for f in ("y", "u", "p"):
+        assert rel(got[f], want[f]) < 1e-6, (f, rel(got[f], want[f]))
+
+
+@pytest.mark.parametrize("n", [5, 9, 17])
+def test_poisson_3d(n):
+    wl = W.workload_c3(n=n)
+    k = _iters_to(wl, 1e-10)
+    got, want, rep, _, _ = _run_pair(wl, k)
+    for f in ("y", "u", "p"):
+        assert rel(got[f], want[f]) < 1e-8, (f, rel(got[f], want[f]))
+
+
+def test_single_unknown_and_tiny_grids():
+    for n in (3, 5):
+        wl = W.workload_c1(n=n)
+        got, want, rep, _, _ = _run_pair(wl, 12)
+        for f in ("y", "u", "p"):
+            assert rel(got[f], want[f]) < 1e-8
+
+
+def test_nodal_bounds_and_dirichlet_data():
+    """Nodal bound arrays, an active lower state bound and non-zero boundary data g."""
+    n = 17
+    x, y = W.node_coords(2, n)
+    ua = -1.0 - x
+    ub = 1.0 + y
+    g = 0.1 * np.sin(np.pi * x)  # boundary values used
+    yd = W.yd_sin_product(n)
+    qp = Q.build(2, n, 1e-3, 1e-3, ua, ub, ya=-0.05, yb=math.inf, yd=-yd, g=g)
+    ref = oipm.solve(qp, n_iter=14)
+    s = ipm.Solver(2, n, 1e-3, 1e-3, ua, ub, -0.05, math.inf)
+    s.set_data(-yd, None, g)
+    s.solve(stop=ipm.STOP_FIXED, fixed_iters=14)
+    assert rel(s.control().reshape(-1), qp.full(ref.u())) < 1e-8
+    assert rel(s.state().reshape(-1), ref.y_full(qp)) < 1e-8
+    assert np.allclose(s.state()[0, :], g[0, :])
+    s.close()
+
+
+def test_paper_stopping_rule_and_report():
+    wl = W.workload_c1()
+    qp = Q.from_workload(wl)
+    ref = oipm.solve(qp, stop="paper")
+    s = ipm.Solver(2, 33, wl.alpha, wl.beta, wl.ua, wl.ub)
+    s.set_data(wl.yd)
+    rep = s.solve()  # paper defaults
+    assert rep["status"] == ipm.OK
+    assert rep["ipm_iters"] == len(ref.history) - 1
+    assert rep["xi_c"] <= 1e-6 and rep["xi_p"] <= 1e-6 and rep["xi_d"] <= 1e-6
+    s.close()
+
+
+def test_deterministic_and_device_io():
+    torch = torch_cuda()
+    wl = W.workload_c2(n=65, cell=4)
+    s = ipm.Solver(2, 65, wl.alpha, wl.beta, wl.ua, wl.ub, wl.ya, wl.yb)
+    s.set_data_device(dev(wl.yd))
+    s.solve(stop=ipm.STOP_KKT, kkt_tol=1e-8)
+    u1 = s.control()
+    s.set_data(wl.yd)
+    s.solve(stop=ipm.STOP_KKT, kkt_tol=1e-8)
+    u2 = s.control()
+    assert np.array_equal(u1, u2)
+    out = torch.empty(65 * 65, dtype=torch.float64, device="cuda")
+    s.get_device("control", out)
+    assert np.array_equal(host(out).reshape(65, 65), u2)
+    s.close()
+
+
+def test_errors_are_reported():
+    with pytest.raises(ipm.IpmError) as e:
+        ipm.Solver(2, 30, 1e-2, 1e-3, -1.0, 1.0)
+    assert e.value.code == ipm.EINVAL
+    with pytest.raises(ipm.IpmError) as e:
+        ipm.Solver(2, 17, 1e-2, 1e-3, 0.0, 1.0)
+    assert e.value.code == ipm.EINVAL
+    with pytest.raises(ipm.IpmError) as e:
+        ipm.Solver(2, 17, 0.0, 1e-3, -1.0, 1.0)
+    assert e.value.code == ipm.EINVAL
+    s = ipm.Solver(2, 17, 1e-2, 1e-3, -1.0, 1.0)
+    with pytest.raises(ipm.IpmError) as e:
+        s.solve()
+    assert e.value.code == ipm.ESTATE
+    with pytest.raises(ipm.IpmError) as e:
+        s.state()
+    assert e.value.code == ipm.ESTATE
+    s.set_data(W.yd_sin_product(17))
+    rep = s.solve(max_ipm=2)
+    assert rep["status"] == ipm.ENOTCONV and rep["ipm_iters"] == 2
+    s.close()
