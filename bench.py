@@ -113,7 +113,7 @@ from oracle import qp as Q, ipm
 wl = W.workload_c2(n={SAMPLE_N}, cell={cell})
 t = time.perf_counter()
 qp = Q.from_workload(wl)
-r = ipm.solve(qp, sigma=wl.sigma, stop="kkt", kkt_tol=1e-6)
+r = ipm.solve(qp, sigma=wl.sigma, stop="kkt", kkt_tol=1e-6, common_step=True)
 dt = time.perf_counter() - t
 print(json.dumps(dict(seconds=dt, iters=len(r.history) - 1, kkt=r.history[-1]["kkt_rel"])))
 """
@@ -188,7 +188,8 @@ def run_ours(args, rank, world):
 
     def opts(prec):
         return ipm.default_options(precision=prec, krylov=ipm.KRYLOV_GMRES_PT, stop=ipm.STOP_KKT,
-                                   kkt_tol=1e-6, restart=50, max_krylov=200)
+                                   kkt_tol=1e-6, restart=50, max_krylov=200, common_step=1,
+                                   max_ipm=60)
 
     def timed(prec, steps, warmup, e2e=False, profile=False):
         o = opts(prec)
@@ -272,6 +273,7 @@ def run_ours(args, rank, world):
         "vs_baseline": None, "dtype": "f64+f32 (mixed: FP32 multigrid/Chebyshev, FP64 Krylov/IPM)",
         "data": "synthetic",
         "config": {"workload": workload_desc(n), "precision": "mixed", "krylov": "FGMRES + P_T",
+                   "ipm": "Algorithm A.1, sigma 0.2, mu0 1, common primal-dual step length",
                    "cells_per_rank": len(cells), "parallelism": f"replicas x{world}",
                    "l2": "per-solve working set (Krylov basis ~3.5 GB) exceeds L2"},
         "latency_ms": {"p50": pct(lat_mx, 50), "p99": pct(lat_mx, 99)},

@@ -90,7 +90,9 @@ enum { IPM_STOP_PAPER = 0, IPM_STOP_KKT = 1, IPM_STOP_FIXED = 2 };
  *              (Algorithm A.1); IPM_STOP_KKT: kkt_rel <= kkt_tol; IPM_STOP_FIXED:
  *              exactly fixed_iters IPM iterations.
  *   kkt_rel = max( ||xi_p|| / (1 + ||f|| + ||M y_d||), ||xi_d|| / (1 + ||M y_d|| + beta ||D 1||),
- *                  mean complementarity product / (1 + |Q(y, z)|) ).                       */
+ *                  mean complementarity product / (1 + |Q(y, z)|) ).
+ *   common_step, mu_rule: variants of Algorithm A.1's step-length and barrier
+ *              updates (defaults 0 = as printed in the paper).                          */
 typedef struct {
   int precision;
   int krylov;
@@ -99,6 +101,8 @@ typedef struct {
   int cheb_steps, vcycles, smooth_pre, smooth_post;
   int max_ipm, max_krylov, restart, fixed_iters;
   double time_limit_s; /* <= 0: none */
+  int common_step; /* 0: separate alpha_P, alpha_D (Algorithm A.1); 1: both = min(alpha_P, alpha_D) */
+  int mu_rule;     /* 0: mu <- sigma mu (Algorithm A.1); 1: mu <- sigma * mean complementarity product */
 } ipm_options;
 
 typedef struct {

@@ -150,20 +150,25 @@ def newton_rhs(qp: QP, s: State, mu: float):
 
 
 def solve_direct(A: sp.csc_matrix, b: np.ndarray, refine: int = 2) -> np.ndarray:
-    """Sparse LU solve with ``refine`` steps of iterative refinement.
+    """Sparse LU solve of A x = b with ``refine`` steps of iterative refinement.
 
-    Symmetric-mode ordering with a small diagonal pivot threshold keeps the fill of
-    the saddle-point factorisation near its structural minimum; the refinement
-    steps restore the residual lost to the relaxed pivoting."""
+    The matrix is first equilibrated symmetrically, S A S with S = diag(1/sqrt(max_j |a_ij|)),
+    then factorised with a symmetric-mode minimum-degree ordering and a small diagonal
+    pivot threshold; this keeps the fill near its structural minimum although Theta spans
+    many orders of magnitude. Refinement runs on the unscaled system."""
+    rmax = np.asarray(abs(A).max(axis=1).todense()).ravel()
+    sc = 1.0 / np.sqrt(np.maximum(rmax, 1e-300))
+    S = sp.diags(sc)
+    As = (S @ A @ S).tocsc()
     try:
-        lu = spla.splu(A, permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.01,
+        lu = spla.splu(As, permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.01,
                        options=dict(SymmetricMode=True))
     except RuntimeError:
         # a zero pivot under relaxed pivoting: fall back to partial pivoting
-        lu = spla.splu(A, permc_spec="MMD_AT_PLUS_A")
-    x = lu.solve(b)
+        lu = spla.splu(As, permc_spec="MMD_AT_PLUS_A")
+    x = sc * lu.solve(sc * b)
     for _ in range(refine):
-        x = x + lu.solve(b - A @ x)
+        x = x + sc * lu.solve(sc * (b - A @ x))
     return x
 
 
@@ -253,12 +258,19 @@ def _record(qp: QP, s: State, k: int, extra: dict) -> dict:
 def solve(qp: QP, sigma: float = 0.2, alpha0: float = 0.995, mu0: float = 1.0,
           eps_p: float = 1e-6, eps_d: float = 1e-6, eps_c: float = 1e-6,
           stop: str = "paper", kkt_tol: float = 1e-6, max_iter: int = 200,
-          n_iter: Optional[int] = None, refine: int = 2) -> Result:
+          n_iter: Optional[int] = None, refine: int = 2, mu_rule: str = "schedule",
+          common_step: bool = False) -> Result:
     """Run Algorithm A.1.
 
     stop = "paper": ||xi_p|| <= eps_p and ||xi_d|| <= eps_d and ||xi_c|| <= eps_c;
     stop = "kkt":   kkt_rel <= kkt_tol;
     n_iter given:   exactly that many iterations (for trajectory comparisons).
+
+    mu_rule = "schedule": mu^{k+1} = sigma mu^k as printed in Algorithm A.1 (default);
+    mu_rule = "gap":      mu^{k+1} = sigma * (mean complementarity product of the current
+                          iterate), the duality-measure form of the path-following scheme
+                          the paper cites; it equals the schedule while full steps are taken.
+    common_step = True:   both primal and dual variables move with min(alpha_P, alpha_D).
     """
     n = qp.nI
     s = initial_state(qp, mu0)
@@ -281,7 +293,11 @@ def solve(qp: QP, sigma: float = 0.2, alpha0: float = 0.995, mu0: float = 1.0,
                 break
         if k >= max_iter:
             break
-        mu = sigma * s.mu
+        if mu_rule == "gap":
+            _, _, _, prods = residuals(qp, s)
+            mu = sigma * float(prods.mean())
+        else:
+            mu = sigma * s.mu
         th_y, th_w, th_v = thetas(qp, s)
         A = newton_matrix(qp, th_y, th_w, th_v)
         b = newton_rhs(qp, s, mu)
@@ -301,6 +317,8 @@ def solve(qp: QP, sigma: float = 0.2, alpha0: float = 0.995, mu0: float = 1.0,
                                       np.full(m.sum(), np.inf)))
         aP *= alpha0
         aD *= alpha0
+        if common_step:
+            aP = aD = min(aP, aD)
         s.y = s.y + aP * dy
         s.w = s.w + aP * dw
         s.v = s.v + aP * dv

@@ -281,9 +281,10 @@ __global__ void k_steplen(GridDesc g, IpmBounds b, IpmState s, const double* __r
   }
 }
 
-// alpha_P = alpha_0 min(1, min ratio), alpha_D likewise -> sc[0], sc[1]
+// alpha_P = alpha_0 min(1, min ratio), alpha_D likewise -> sc[0], sc[1]; with `common`
+// both take the smaller value.
 __global__ void k_steplen_final(const double* __restrict__ part, long long nb, double alpha0,
-                                double* __restrict__ sc) {
+                                int common, double* __restrict__ sc) {
   __shared__ double sh[32];
   double aP = 1e300, aD = 1e300;
   for (long long t = threadIdx.x; t < nb; t += blockDim.x) {
@@ -293,8 +294,10 @@ __global__ void k_steplen_final(const double* __restrict__ part, long long nb, d
   aP = block_min(aP, sh);
   aD = block_min(aD, sh);
   if (threadIdx.x == 0) {
-    sc[0] = alpha0 * fmin(1.0, aP);
-    sc[1] = alpha0 * fmin(1.0, aD);
+    double p = alpha0 * fmin(1.0, aP), d = alpha0 * fmin(1.0, aD);
+    if (common) p = d = fmin(p, d);
+    sc[0] = p;
+    sc[1] = d;
   }
 }
 
@@ -472,11 +475,11 @@ void launch_prep(const GridDesc& g, const IpmProblem& pb, const IpmBounds& b, Ip
                                                         mu, rhs, write32);
 }
 void launch_steplen(const GridDesc& g, const IpmBounds& b, IpmState st, const double* dx,
-                    double mu, double alpha0, double* part, double* sc, cudaStream_t s) {
+                    double mu, double alpha0, int common, double* part, double* sc, cudaStream_t s) {
   count_launches(1);
   k_steplen<<<interior_grid(g), interior_block(), 0, s>>>(g, b, st, dx, mu, part);
   count_launches(1);
-  k_steplen_final<<<1, 256, 0, s>>>(part, interior_blocks(g), alpha0, sc);
+  k_steplen_final<<<1, 256, 0, s>>>(part, interior_blocks(g), alpha0, common, sc);
 }
 void launch_update(const GridDesc& g, const IpmBounds& b, IpmState st, const double* dx,
                    double mu, const double* sc, cudaStream_t s) {

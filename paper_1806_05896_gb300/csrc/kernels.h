@@ -57,7 +57,7 @@ void launch_init_state(const GridDesc& g, const IpmBounds& b, IpmState st, doubl
 void launch_prep(const GridDesc& g, const IpmProblem& pb, const IpmBounds& b, IpmState st,
                  IpmDiag dg, double mu, double* rhs, int write32, cudaStream_t s);
 void launch_steplen(const GridDesc& g, const IpmBounds& b, IpmState st, const double* dx,
-                    double mu, double alpha0, double* part, double* sc, cudaStream_t s);
+                    double mu, double alpha0, int common, double* part, double* sc, cudaStream_t s);
 void launch_update(const GridDesc& g, const IpmBounds& b, IpmState st, const double* dx,
                    double mu, const double* sc, cudaStream_t s);
 void launch_residuals(const GridDesc& g, const IpmProblem& pb, const IpmBounds& b, IpmState st,

@@ -83,6 +83,7 @@ struct ipm_solver {
   long long prof_count = 0;
 
   double c0 = 0, ncy = 0, nf = 0, nd = 0, nbounds = 0;
+  double mean_prod = 0;  // mean complementarity product of the current iterate
   bool has_data = false, solved = false;
   std::vector<double> hist;  // rows of kHistCols
   std::string err;
@@ -640,7 +641,8 @@ struct ipm_solver {
     double Q = 0.5 * (q[4] - 2.0 * q[5] + c0) + 0.5 * alpha * q[6] + beta * lumped_mass(g) * q[7];
     double rp = xp / (1.0 + nf + ncy);
     double rd = xd / (1.0 + ncy + beta * nd);
-    double rc = nbounds > 0 ? (q[3] / nbounds) / (1.0 + std::fabs(Q)) : 0.0;
+    mean_prod = nbounds > 0 ? q[3] / nbounds : 0.0;
+    double rc = mean_prod / (1.0 + std::fabs(Q));
     double kkt = std::max(rp, std::max(rd, rc));
     double row[kHistCols] = {(double)k, mu, xp, xd, xc, kkt, aP, aD, (double)kit, krr};
     hist.insert(hist.end(), row, row + kHistCols);
@@ -651,7 +653,7 @@ struct ipm_solver {
     if (o.restart < 1 || o.restart > kMaxRestart) throw IpmError{IPM_EINVAL, "restart out of range [1, 100]"};
     if (o.cheb_steps < 1 || o.vcycles < 1 || o.smooth_pre < 0 || o.smooth_post < 0 ||
         !(o.sigma > 0 && o.sigma < 1) || !(o.alpha0 > 0 && o.alpha0 < 1) || !(o.mu0 > 0) ||
-        o.max_krylov < 1 || o.max_ipm < 0)
+        o.max_krylov < 1 || o.max_ipm < 0 || o.mu_rule < 0 || o.mu_rule > 1)
       throw IpmError{IPM_EINVAL, "invalid solver options"};
     if (o.smooth_pre != o.smooth_post && o.krylov == IPM_KRYLOV_MINRES_PD)
       throw IpmError{IPM_EINVAL, "MINRES needs a symmetric V-cycle (smooth_pre == smooth_post)"};
@@ -679,7 +681,7 @@ struct ipm_solver {
         status = IPM_ETIMEOUT;
         break;
       }
-      mu *= o.sigma;
+      mu = o.mu_rule == 1 ? o.sigma * mean_prod : o.sigma * mu;
       launch_prep(g, problem(), bounds(), st, dg, mu, rhs, o.precision == IPM_PREC_MIXED, stream);
       setup_precond(o);
       int kit = 0;
@@ -687,7 +689,7 @@ struct ipm_solver {
       krylov(o, rhs, dx, &kit, &krr);
       ktot += kit;
       krr_max = std::max(krr_max, krr);
-      launch_steplen(g, bounds(), st, dx, mu, o.alpha0, part, sc, stream);
+      launch_steplen(g, bounds(), st, dx, mu, o.alpha0, o.common_step, part, sc, stream);
       launch_update(g, bounds(), st, dx, mu, sc, stream);
       ++k;
       fetch(sc, 2);
@@ -773,6 +775,8 @@ void ipm_default_options(ipm_options* o) {
   o->restart = 50;
   o->fixed_iters = 0;
   o->time_limit_s = 0.0;
+  o->common_step = 0;
+  o->mu_rule = 0;
 }
 
 int ipm_create(const ipm_grid* grid, const ipm_pde* pde, double alpha, double beta,

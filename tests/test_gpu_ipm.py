@@ -19,12 +19,13 @@ from gpu_util import dev, host, rel, torch_cuda
 pytestmark = pytest.mark.gpu
 
 
-def _run_pair(wl, k, **opts):
+def _run_pair(wl, k, common=False, **opts):
     qp = Q.from_workload(wl)
-    ref = oipm.solve(qp, sigma=wl.sigma, n_iter=k)
+    ref = oipm.solve(qp, sigma=wl.sigma, n_iter=k, common_step=common)
     s = ipm.Solver(wl.dim, wl.n, wl.alpha, wl.beta, wl.ua, wl.ub, wl.ya, wl.yb)
     s.set_data(wl.yd)
-    rep = s.solve(stop=ipm.STOP_FIXED, fixed_iters=k, sigma=wl.sigma, **opts)
+    rep = s.solve(stop=ipm.STOP_FIXED, fixed_iters=k, sigma=wl.sigma, common_step=int(common),
+                  **opts)
     got = dict(y=s.state().reshape(-1), u=s.control().reshape(-1), p=s.adjoint().reshape(-1))
     want = dict(y=ref.y_full(qp), u=qp.full(ref.u()), p=qp.full(ref.state.p))
     hist = s.history()
@@ -32,9 +33,10 @@ def _run_pair(wl, k, **opts):
     return got, want, rep, hist, ref
 
 
-def _iters_to(wl, tol):
+def _iters_to(wl, tol, common=False):
     qp = Q.from_workload(wl)
-    r = oipm.solve(qp, sigma=wl.sigma, stop="kkt", kkt_tol=tol)
+    r = oipm.solve(qp, sigma=wl.sigma, stop="kkt", kkt_tol=tol, max_iter=40, common_step=common)
+    assert r.converged
     return len(r.history) - 1
 
 
@@ -54,24 +56,40 @@ def test_poisson_33_fp64(krylov):
             assert abs(a["alpha_P"] - b["alpha_P"]) < 1e-8 and abs(a["alpha_D"] - b["alpha_D"]) < 1e-8
 
 
-@pytest.mark.parametrize("cell", [0, 1, 2, 3, 4, 5])
-def test_gaussian_state_bound_65(cell):
-    """y <= 0.1, Gaussian-sum y_d, u in [-30, 30] (the 1025^2 sweep's recipe at 65^2), alpha >= 1e-4."""
+@pytest.mark.parametrize("cell,common", [(0, False), (1, False), (2, False), (0, True), (3, True),
+                                         (4, True), (5, True)])
+def test_gaussian_state_bound_65(cell, common):
+    """y <= 0.1, Gaussian-sum y_d, u in [-30, 30] (the 1025^2 sweep's recipe at 65^2), alpha >= 1e-4,
+    with Algorithm A.1's separate step lengths and with the common-step variant."""
     wl = W.workload_c2(n=65, cell=cell)
-    k = _iters_to(wl, 1e-10)
-    got, want, rep, _, _ = _run_pair(wl, k)
+    k = _iters_to(wl, 1e-10, common)
+    got, want, rep, _, _ = _run_pair(wl, k, common)
     for f in ("y", "u", "p"):
         assert rel(got[f], want[f]) < 1e-8, (f, rel(got[f], want[f]))
     assert got["y"].max() <= 0.1
 
 
-@pytest.mark.parametrize("cell", [1, 4, 7])
+@pytest.mark.parametrize("cell", [1, 4, 6])
 def test_mixed_precision_gaussian_65(cell):
     wl = W.workload_c2(n=65, cell=cell)
-    k = _iters_to(wl, 1e-6)
-    got, want, rep, _, _ = _run_pair(wl, k, precision=ipm.PREC_MIXED)
+    k = _iters_to(wl, 1e-6, True)
+    got, want, rep, _, _ = _run_pair(wl, k, True, precision=ipm.PREC_MIXED)
     for f in ("y", "u", "p"):
         assert rel(got[f], want[f]) < 1e-6, (f, rel(got[f], want[f]))
+
+
+def test_gap_mu_rule_matches_oracle():
+    wl = W.workload_c2(n=33, cell=3)
+    qp = Q.from_workload(wl)
+    ref = oipm.solve(qp, sigma=wl.sigma, n_iter=12, mu_rule="gap", common_step=True)
+    s = ipm.Solver(2, 33, wl.alpha, wl.beta, wl.ua, wl.ub, wl.ya, wl.yb)
+    s.set_data(wl.yd)
+    s.solve(stop=ipm.STOP_FIXED, fixed_iters=12, mu_rule=1, common_step=1)
+    h = s.history()
+    for a, b in zip(h, ref.history):
+        assert abs(a["mu"] - b["mu"]) <= 1e-9 * b["mu"]
+    assert rel(s.control().reshape(-1), qp.full(ref.u())) < 1e-8
+    s.close()
 
 
 @pytest.mark.parametrize("n", [5, 9, 17])

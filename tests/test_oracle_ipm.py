@@ -43,6 +43,19 @@ def test_ipm_matches_brute_force(n, amp, alpha, beta):
     assert _rel(r.state.p, p_bf) < 1e-9
 
 
+@pytest.mark.parametrize("mu_rule,common", [("gap", False), ("schedule", True), ("gap", True)])
+def test_ipm_variants_reach_the_same_optimum(mu_rule, common):
+    """The step-length / barrier-update variants change the path, not the unique optimum."""
+    ua, ub = -2.0, 1.5
+    qp = Q.build(2, 9, 1e-3, 1e-3, ua, ub, yd=_yd_mixed(9, 0.3))
+    _, u_bf, _, _ = brute.solve(qp, np.full(qp.nI, ua), np.full(qp.nI, ub))
+    r = ipm.solve(qp, stop="kkt", kkt_tol=1e-14, max_iter=60, mu_rule=mu_rule, common_step=common)
+    assert r.converged
+    assert _rel(r.u(), u_bf) < 1e-7
+    if common:
+        assert all(h["alpha_P"] == h["alpha_D"] for h in r.history[1:])
+
+
 def test_beta_zero_matches_linear_kkt():
     qp = Q.build(2, 9, 1e-2, 0.0, -50.0, 50.0, yd=W.yd_sin_product(9))
     y, u, p = linear_kkt.solve(qp)
