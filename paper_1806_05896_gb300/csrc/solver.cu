@@ -59,6 +59,7 @@ struct ipm_solver {
   IpmState st{};
   double *ya = nullptr, *yb = nullptr, *zbw = nullptr, *zbv = nullptr;
   double *cy = nullptr, *fvec = nullptr, *glift = nullptr;
+  double *ydbuf = nullptr, *fbuf = nullptr;  // packed nodal y_d and f (boundary included)
   IpmDiag dg{};
   double *rhs = nullptr, *dx = nullptr, *ktmp = nullptr;
   double *V = nullptr, *Z = nullptr;
@@ -235,6 +236,8 @@ struct ipm_solver {
     cy = alloc<double>(f);
     fvec = alloc<double>(f);
     glift = alloc<double>(f);
+    ydbuf = alloc<double>(f);
+    fbuf = alloc<double>(f);
     dg.thy = alloc<double>(f);
     dg.thw = alloc<double>(f);
     dg.thv = alloc<double>(f);
@@ -297,9 +300,10 @@ struct ipm_solver {
   }
 
   void set_data(const double* yd, const double* f, const double* gb, bool device) {
-    // pack y_d -> rhs[0:F] (scratch), f -> rhs[F:2F], g -> glift (boundary only)
-    double* ydp = rhs;
-    double* fp = rhs + F();
+    // pack y_d and f with their boundary values into their own buffers (never into
+    // Krylov vectors, whose boundary entries must stay zero), g -> glift (boundary only)
+    double* ydp = ydbuf;
+    double* fp = fbuf;
     auto put = [&](const double* src, double* dst, int mode) {
       if (!src) {
         launch_pack(g, nullptr, dst, mode, stream);
