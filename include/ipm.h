@@ -203,6 +203,26 @@ int ipm_vcycle_device(ipm_solver* s, const ipm_options* opt, int transpose, cons
 int ipm_newton_step_device(ipm_solver* s, const ipm_options* opt, const double* const* iterate,
                            double mu, double* dx, int* iters, double* relres);
 
+/* Allocation-free Chebyshev semi-iteration (the paper has no counterpart: this
+ * entry point exists for callers that cannot let a library call cudaMalloc, e.g.
+ * applications that hand out all device memory from their own pool, or service
+ * loops where an allocation and the synchronisation it may imply would stall
+ * other work). Same result as ipm_chebyshev_device: x = `steps` steps of
+ * Chebyshev semi-iteration for (M + Theta_y) x = b on the Q1 grid of n^dim nodes,
+ * FP64. theta_y, b, x: device arrays of n^dim doubles (dense, boundary included,
+ * x fastest); x gets a zero boundary and must not alias theta_y or b. Work is
+ * enqueued on `stream` (NULL = legacy default stream).
+ * Work vectors live in one fixed device array of 3 * 274625 doubles (6.3 MiB)
+ * that every GPU loading the library keeps until the process exits; grids with
+ * n^dim > 274625 (beyond 65^3, 513^2) are rejected with IPM_EINVAL. The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress)
+ * with the device current; make that first call before any stream capture.
+ * All calls share the array and each clears the part it uses: calls that overlap
+ * on the GPU (different streams, or host threads racing) corrupt each other.
+ * No cudaMalloc, cudaFree or allocating library routine is called. */
+int ipm_chebyshev_noalloc(int dim, int n, int steps, const double* theta_y, const double* b,
+                          double* x, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,94 @@
+// Chebyshev semi-iteration for (M + Theta_y) x = b that allocates no device memory.
+//
+// Some callers cannot let a library call cudaMalloc: applications that own all
+// device memory through their own pool and cap what third-party code may take,
+// or service loops where an allocation (and the device-wide synchronisation it
+// may imply) would stall other work. This entry point keeps its work vectors in
+// one file-scope device array of fixed size instead; every GPU that loads the
+// library holds that array until the process exits.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "ipm.h"
+#include "kernels.h"
+
+namespace {
+
+// Largest grid served: n^d <= 274625 nodes (65^3; also covers 2D grids up to 513^2).
+constexpr long long kNoAllocMaxNodes = 274625;
+
+// Three work vectors: the current and previous Chebyshev iterates and a copy of b.
+// 3 * 274625 * 8 bytes = 6.3 MiB per device.
+static __device__ __align__(256) double g_cheb_scratch[3 * kNoAllocMaxNodes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+double* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_cheb_scratch on the current device. In host code the symbol
+// name is only a host-side stand-in, so the address is looked up once per device,
+// with that device current, and cached.
+int scratch_address(double** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return IPM_ECUDA;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_cheb_scratch) != cudaSuccess) {
+      cudaGetLastError();
+      return IPM_ECUDA;
+    }
+    g_scratch_addr[dev] = (double*)p;
+  }
+  *out = g_scratch_addr[dev];
+  return IPM_OK;
+}
+
+}  // namespace
+
+extern "C" int ipm_chebyshev_noalloc(int dim, int n, int steps, const double* theta_y,
+                                     const double* b, double* x, void* stream) {
+  if ((dim != 2 && dim != 3) || n < 3 || steps < 1 || !theta_y || !b || !x) return IPM_EINVAL;
+  long long nodes = (long long)n * n * (dim == 3 ? n : 1);
+  if (nodes > kNoAllocMaxNodes) return IPM_EINVAL;  // beyond the fixed work array
+  double* work = nullptr;
+  int rc = scratch_address(&work);
+  if (rc != IPM_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  // dense layout (pitch = n) so the caller's arrays are read and written in place
+  GridDesc g;
+  g.dim = dim;
+  g.n = n;
+  g.pitch = n;
+  g.plane = (long long)n * n;
+  g.field = nodes;
+  g.h = 1.0 / (n - 1);
+  double* bT = work;
+  double* cur = work + nodes;
+  double* prev = work + 2 * nodes;
+  // The array keeps the previous call's contents (possibly for another grid):
+  // the iterates' boundary entries must read as zero, so clear the used part.
+  if (cudaMemsetAsync(work, 0, sizeof(double) * 3 * nodes, s) != cudaSuccess) return IPM_ECUDA;
+  const double lmin = dim == 2 ? 0.25 : 0.125, lmax = dim == 2 ? 2.25 : 3.375;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sig = theta / delta;
+  const double dM = dim == 2 ? (2.0 * g.h / 3.0) * (2.0 * g.h / 3.0)
+                             : (2.0 * g.h / 3.0) * (2.0 * g.h / 3.0) * (2.0 * g.h / 3.0);
+  if (cudaMemsetAsync(x, 0, sizeof(double) * nodes, s) != cudaSuccess) return IPM_ECUDA;
+  launch_cheb_init<double>(g, b, theta_y, dM, 1.0 / theta, bT, cur, prev, s);
+  double rho = 1.0 / sig;
+  for (int k = 1; k < steps; ++k) {
+    double rho_new = 1.0 / (2.0 * sig - rho);
+    double om = 2.0 * sig * rho_new;
+    rho = rho_new;
+    double* out = k == steps - 1 ? x : prev;
+    launch_cheb_step<double, double>(g, cur, prev, bT, theta_y, dM, om, 1.0 / theta, out, s);
+    if (k < steps - 1) {
+      double* t = cur;
+      cur = prev;
+      prev = t;
+    }
+  }
+  if (steps == 1) launch_convert<double, double>(g, cur, x, s);
+  return cudaGetLastError() == cudaSuccess ? IPM_OK : IPM_ECUDA;
+}

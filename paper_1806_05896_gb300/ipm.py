@@ -32,7 +32,7 @@ EXPORTED = (
     "ipm_get_history", "ipm_destroy", "ipm_launch_count",
     "ipm_profile_smoother", "ipm_profile_read", "ipm_strerror", "ipm_last_error",
     "ipm_newton_apply_device", "ipm_precond_apply_device", "ipm_chebyshev_device",
-    "ipm_vcycle_device", "ipm_newton_step_device",
+    "ipm_vcycle_device", "ipm_newton_step_device", "ipm_chebyshev_noalloc",
 )
 
 
@@ -116,6 +116,7 @@ def load() -> C.CDLL:
     lib.ipm_vcycle_device.argtypes = [P, C.POINTER(Options), C.c_int, P, P, P]
     lib.ipm_newton_step_device.argtypes = [P, C.POINTER(Options), C.POINTER(P), C.c_double, P,
                                            C.POINTER(C.c_int), D]
+    lib.ipm_chebyshev_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P]
     _lib = lib
     return lib
 
@@ -149,6 +150,14 @@ def _hptr(a):
         return None
     a = np.ascontiguousarray(a, dtype=np.float64)
     return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def chebyshev_noalloc(dim: int, n: int, steps: int, th_y, b, x, stream: Optional[int] = None):
+    """Allocation-free Chebyshev semi-iteration (fixed device work array, n^dim <= 274625)."""
+    rc = load().ipm_chebyshev_noalloc(dim, n, steps, _dptr(th_y), _dptr(b), _dptr(x), stream)
+    if rc != OK:
+        raise IpmError(rc, load().ipm_strerror(rc).decode())
+    return x
 
 
 class Solver:
