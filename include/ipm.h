@@ -103,6 +103,8 @@ typedef struct {
   double time_limit_s; /* <= 0: none */
   int common_step; /* 0: separate alpha_P, alpha_D (Algorithm A.1); 1: both = min(alpha_P, alpha_D) */
   int mu_rule;     /* 0: mu <- sigma mu (Algorithm A.1); 1: mu <- sigma * mean complementarity product */
+  int kernel_flags; /* 0: fastest kernels; bit 0: per-sweep multigrid/Chebyshev kernels instead of
+                       the fused 2D ones; bit 1: no CUDA-graph replay of Krylov iterations */
 } ipm_options;
 
 typedef struct {

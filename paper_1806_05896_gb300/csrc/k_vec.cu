@@ -133,6 +133,23 @@ __global__ void k_lincomb3(double* __restrict__ y, double a, const double* __res
 }
 }  // namespace
 
+namespace {
+// y = x / sqrt(s[0])  (normalisation by a device-side squared norm)
+__global__ void k_scale_rsqrt(double* y, const double* x, const double* __restrict__ s,
+                              long long len) {
+  double f = 1.0 / sqrt(s[0]);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
+       e += (long long)gridDim.x * blockDim.x)
+    y[e] = x[e] * f;
+}
+}  // namespace
+
+void launch_scale_rsqrt(double* y, const double* x, const double* s, long long len,
+                        cudaStream_t st) {
+  count_launches(1);
+  k_scale_rsqrt<<<vec_blocks(len), 256, 0, st>>>(y, x, s, len);
+}
+
 void launch_lincomb3(double* y, double a, const double* x1, double b, const double* x2, double c,
                      const double* x3, long long len, cudaStream_t s) {
   count_launches(1);

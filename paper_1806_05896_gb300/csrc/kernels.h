@@ -109,6 +109,45 @@ template <typename T>
 void launch_mg_zero(const GridDesc& g, T* x, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
+// k_mg_fused.cu (2D Poisson: tiled multi-sweep kernels and a one-CTA coarse cycle)
+// ----------------------------------------------------------------------------
+constexpr int kMaxCoarse = 8;
+template <typename T>
+struct MGCoarse {  // levels handled inside one CTA, finest first
+  int nl;
+  int n[kMaxCoarse];
+  long long pitch[kMaxCoarse];
+  const T* m[kMaxCoarse];
+};
+template <typename T>
+size_t mg2_coarse_smem(const MGCoarse<T>& cl);
+template <typename T>
+void launch_mg2_pre_restrict(const GridDesc& g, const GridDesc& gc, const T* xin, T* xout,
+                             const T* b, const T* m, T* bc, double omega, int nu, int zero_init,
+                             cudaStream_t s);
+template <typename T>
+void launch_mg2_prolong_post(const GridDesc& g, const GridDesc& gc, const T* xin, const T* xc,
+                             T* xout, const T* b, const T* m, double omega, int nu,
+                             cudaStream_t s);
+template <typename T>
+void launch_mg2_coarse(const MGCoarse<T>& cl, const T* btop, T* xtop, double omega, int nu_pre,
+                       int nu_post, cudaStream_t s);
+
+// Temporally blocked Chebyshev (2D): `ns` steps per launch with step weights omega[0..ns)
+constexpr int kMaxChebBlock = 8;
+struct ChebSteps {
+  int ns;
+  double omega[kMaxChebBlock];
+  double gamma;   // 1 / theta
+  double dM;      // diag(M)
+  double mscale;  // h^2 / 36
+};
+template <typename T, typename Ti, typename To>
+void launch_cheb2_block(const GridDesc& g, const ChebSteps& cs, const Ti* b, const T* thy,
+                        const T* xc_in, const T* xp_in, T* xc_out, T* xp_out, To* final_out,
+                        int first, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
 // k_vec.cu (Krylov vector kernels over whole field blocks, deterministic)
 // ----------------------------------------------------------------------------
 void launch_multidot(const double* V, long long stride, int nv, const double* w, long long len,
@@ -122,6 +161,8 @@ void launch_axpy_dev(double* y, const double* x, const double* a, double sign, l
                      cudaStream_t s);
 void launch_dot(const double* a, const double* b, long long len, double* part, double* out,
                 cudaStream_t s);
+void launch_scale_rsqrt(double* y, const double* x, const double* s, long long len,
+                        cudaStream_t st);
 void launch_lincomb3(double* y, double a, const double* x1, double b, const double* x2, double c,
                      const double* x3, long long len, cudaStream_t s);
 void launch_mhat(const GridDesc& g, double alpha, double dM, const double* thy, const double* thw,

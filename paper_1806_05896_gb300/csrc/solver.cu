@@ -65,8 +65,8 @@ struct ipm_solver {
   double *V = nullptr, *Z = nullptr;
   int vcap = 0;
   double* mr[14] = {};
-  double* cheb64[3] = {};
-  float* cheb32[3] = {};
+  double* cheb64[4] = {};
+  float* cheb32[4] = {};
   MGHier<double> mg64;
   MGHier<float> mg32;
   double *part = nullptr, *dout = nullptr, *sc = nullptr, *kdev = nullptr;
@@ -86,6 +86,15 @@ struct ipm_solver {
   double c0 = 0, ncy = 0, nf = 0, nd = 0, nbounds = 0;
   double mean_prod = 0;  // mean complementarity product of the current iterate
   bool has_data = false, solved = false;
+  bool fused = true;  // use the fused 2D multigrid kernels
+  int last_precision = IPM_PREC_MIXED;
+  // CUDA graphs of the FGMRES iteration body, one per Arnoldi index j, for one
+  // configuration key (precision, preconditioner, smoothing, stream); a body is
+  // captured the second time it runs (its first, eager run sets kernel attributes)
+  bool use_graphs = true;
+  std::vector<cudaGraphExec_t> gexec;
+  std::vector<int> gruns;
+  long long gkey = -1;
   std::vector<double> hist;  // rows of kHistCols
   std::string err;
 
@@ -141,7 +150,16 @@ struct ipm_solver {
     prof_used += 2;
   }
 
+  void drop_graphs() {
+    for (cudaGraphExec_t e : gexec)
+      if (e) cudaGraphExecDestroy(e);
+    gexec.clear();
+    gruns.clear();
+    gcount.clear();
+  }
+
   void release() {
+    drop_graphs();
     for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
     prof_ev.clear();
     for (void* p : allocs) cudaFree(p);
@@ -247,8 +265,8 @@ struct ipm_solver {
     rhs = alloc<double>(4 * f);
     dx = alloc<double>(4 * f);
     ktmp = alloc<double>(4 * f);
-    for (int i = 0; i < 3; ++i) cheb64[i] = alloc<double>(f);
-    for (int i = 0; i < 3; ++i) cheb32[i] = alloc<float>(f);
+    for (int i = 0; i < 4; ++i) cheb64[i] = alloc<double>(f);
+    for (int i = 0; i < 4; ++i) cheb32[i] = alloc<float>(f);
     build_mg(mg64);
     build_mg(mg32);
     part_rows = std::max<long long>(interior_blocks(g), 8 * kRedBlocks);
@@ -374,18 +392,101 @@ struct ipm_solver {
     }
   }
 
+  // first level handled by the one-CTA coarse kernel (2D Poisson fused path)
+  template <typename T>
+  int coarse_start(const MGHier<T>& mg) const {
+    const int limit = sizeof(T) == 4 ? 65 : 33;
+    for (int l = 0; l < mg.nlev; ++l)
+      if (mg.lv[l].g.n <= limit) return l;
+    return mg.nlev - 1;
+  }
+  bool fused_mg() const { return g.dim == 2 && fused && nu_fits; }
+  bool nu_fits = true;  // fused tiles hold up to 8 sweeps of halo
+
+  // one V-cycle with the fused kernels (same operator, smoother and transfers)
+  template <typename T>
+  void vcycle_fused(MGHier<T>& mg, bool zero_x, const ipm_options& o) {
+    const int lc = coarse_start(mg);
+    for (int l = 0; l < lc; ++l) {
+      MGLevel<T>& L = mg.lv[l];
+      int& cur = mg.cur[l];
+      bool pr = l == 0 && !(zero_x && l == 0) && prof_begin();
+      launch_mg2_pre_restrict<T>(L.g, mg.lv[l + 1].g, L.x[cur], L.x[1 - cur], L.b, L.m,
+                                 mg.lv[l + 1].b, omega(), o.smooth_pre, (l > 0 || zero_x) ? 1 : 0,
+                                 stream);
+      prof_end(pr);
+      cur = 1 - cur;
+    }
+    MGCoarse<T> cl;
+    cl.nl = mg.nlev - lc;
+    for (int l = lc; l < mg.nlev; ++l) {
+      cl.n[l - lc] = mg.lv[l].g.n;
+      cl.pitch[l - lc] = mg.lv[l].g.pitch;
+      cl.m[l - lc] = mg.lv[l].m;
+    }
+    launch_mg2_coarse<T>(cl, mg.lv[lc].b, mg.lv[lc].x[mg.cur[lc]], omega(), o.smooth_pre,
+                         o.smooth_post, stream);
+    for (int l = lc - 1; l >= 0; --l) {
+      MGLevel<T>& L = mg.lv[l];
+      int& cur = mg.cur[l];
+      launch_mg2_prolong_post<T>(L.g, mg.lv[l + 1].g, L.x[cur], mg.lv[l + 1].x[mg.cur[l + 1]],
+                                 L.x[1 - cur], L.b, L.m, omega(), o.smooth_post, stream);
+      cur = 1 - cur;
+    }
+  }
+
   // x = (vcycles V-cycles from zero) applied to lv[0].b; returns the level-0 iterate
   template <typename T>
   T* mg_solve(MGHier<T>& mg, int tr, const ipm_options& o) {
-    for (int c = 0; c < std::max(1, o.vcycles); ++c) vcycle(mg, 0, c == 0, tr, o);
+    for (int c = 0; c < std::max(1, o.vcycles); ++c) {
+      if (fused_mg()) vcycle_fused(mg, c == 0, o);  // L symmetric: tr needs no change
+      else vcycle(mg, 0, c == 0, tr, o);
+    }
     return mg.lv[0].x[mg.cur[0]];
   }
 
   // ------------------------------------------------------------------------
   // Chebyshev semi-iteration for (M + Theta_y) x = r_y (Section 4.1)
   // ------------------------------------------------------------------------
+  // 2D: blocks of up to 5 steps per launch (temporal blocking), same recurrence
+  template <typename T>
+  void cheb_apply_fused(const double* r, const T* thy, double* z, int steps, T* const* buf) {
+    const double lmin = 0.25, lmax = 2.25;
+    double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sig = theta / delta;
+    std::vector<double> om(steps + 1, 0.0);
+    double rho = 1.0 / sig;
+    for (int k = 1; k < steps; ++k) {
+      double rho_new = 1.0 / (2.0 * sig - rho);
+      om[k] = 2.0 * sig * rho_new;
+      rho = rho_new;
+    }
+    ChebSteps cs;
+    cs.gamma = 1.0 / theta;
+    cs.dM = mass_diag(g);
+    cs.mscale = g.h * g.h / 36.0;
+    int k = 1, pair = 0;
+    bool first = true;
+    while (true) {
+      int ns = std::min(5, steps - k);
+      cs.ns = ns;
+      for (int q = 0; q < ns; ++q) cs.omega[q] = om[k + q];
+      bool last = k + ns == steps;
+      launch_cheb2_block<T, double, double>(g, cs, r, thy, buf[2 * pair], buf[2 * pair + 1],
+                                            buf[2 * (1 - pair)], buf[2 * (1 - pair) + 1],
+                                            last ? z : nullptr, first ? 1 : 0, stream);
+      k += ns;
+      first = false;
+      pair = 1 - pair;
+      if (last) break;
+    }
+  }
+
   template <typename T, typename To>
   void cheb_apply(const double* r, const T* thy, To* z, int steps, T* const* buf) {
+    if (g.dim == 2 && fused) {
+      cheb_apply_fused<T>(r, thy, (double*)z, steps, buf);
+      return;
+    }
     double lmin = g.dim == 2 ? 0.25 : 0.125, lmax = g.dim == 2 ? 2.25 : 3.375;
     double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sig = theta / delta;
     T* bT = buf[2];
@@ -460,6 +561,71 @@ struct ipm_solver {
     }
   }
 
+  // One Arnoldi step j of FGMRES, enqueued on the stream (no host synchronisation):
+  // normalise V_j by the squared norm left by step j-1, Z_j = P^{-1} V_j,
+  // V_{j+1} = A Z_j, two classical Gram-Schmidt passes against V_0..V_j, the squared
+  // norm of V_{j+1}, and a copy of the coefficients into the pinned host buffer.
+  void arnoldi_body(const ipm_options& o, int j, long long stride, long long len, int tri) {
+    double* vj = V + (long long)j * stride;
+    double* zj = Z + (long long)j * stride;
+    double* w = V + (long long)(j + 1) * stride;
+    const int K = kMaxRestart + 2;
+    if (j > 0) launch_scale_rsqrt(vj, vj, kdev + 2 * K, len, stream);
+    precond(vj, zj, tri, o);
+    newton_apply(zj, w);
+    launch_multidot(V, stride, j + 1, w, len, part, kdev, stream);
+    launch_axpy_multi(w, V, stride, j + 1, kdev, -1.0, len, stream);
+    launch_multidot(V, stride, j + 1, w, len, part, kdev + K, stream);
+    launch_axpy_multi(w, V, stride, j + 1, kdev + K, -1.0, len, stream);
+    launch_dot(w, w, len, part, kdev + 2 * K, stream);
+    CK(cudaMemcpyAsync(hbuf, kdev, sizeof(double) * (2 * K + 1), cudaMemcpyDeviceToHost, stream));
+  }
+
+  void arnoldi_step(const ipm_options& o, int j, long long stride, long long len, int tri) {
+    long long key = ((long long)o.precision << 40) ^ ((long long)tri << 39) ^
+                    ((long long)o.cheb_steps << 30) ^ ((long long)o.vcycles << 24) ^
+                    ((long long)o.smooth_pre << 16) ^ ((long long)o.smooth_post << 8) ^
+                    ((long long)(fused ? 1 : 0) << 4) ^ (long long)(size_t)stream;
+    bool graphs = use_graphs && !prof_on;
+    if (!graphs) {
+      arnoldi_body(o, j, stride, len, tri);
+      return;
+    }
+    if (key != gkey) {
+      drop_graphs();
+      gkey = key;
+    }
+    if ((int)gexec.size() <= j) {
+      gexec.resize(j + 1, nullptr);
+      gruns.resize(j + 1, 0);
+    }
+    if (!gexec[j] && gruns[j] >= 1) {
+      cudaGraph_t graph = nullptr;
+      long long before = launches_total();
+      CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+      arnoldi_body(o, j, stride, len, tri);
+      CK(cudaStreamEndCapture(stream, &graph));
+      // captured launches do not run now: count them at each replay instead
+      gcount.resize(j + 1, 0);
+      gcount[j] = launches_total() - before;
+      count_launches(-gcount[j]);
+      cudaGraphExec_t ex = nullptr;
+      cudaError_t e = cudaGraphInstantiate(&ex, graph, 0);
+      cudaGraphDestroy(graph);
+      CK(e);
+      gexec[j] = ex;
+    }
+    ++gruns[j];
+    if (gexec[j]) {
+      count_launches(gcount[j]);
+      CK(cudaGraphLaunch(gexec[j], stream));
+    } else {
+      arnoldi_body(o, j, stride, len, tri);
+    }
+  }
+
+  std::vector<long long> gcount;  // kernels inside each captured Arnoldi step
+
   // ------------------------------------------------------------------------
   // Right-preconditioned flexible GMRES with classical Gram-Schmidt applied
   // twice; restarts every o.restart iterations. x0 = 0. The residual estimate
@@ -495,18 +661,7 @@ struct ipm_solver {
       int j = 0;
       bool done = false;
       for (; j < m && total < o.max_krylov; ++j) {
-        double* vj = V + (long long)j * stride;
-        double* zj = Z + (long long)j * stride;
-        double* w = V + (long long)(j + 1) * stride;
-        precond(vj, zj, tri, o);
-        newton_apply(zj, w);
-        launch_multidot(V, stride, j + 1, w, len, part, kdev, stream);
-        launch_axpy_multi(w, V, stride, j + 1, kdev, -1.0, len, stream);
-        launch_multidot(V, stride, j + 1, w, len, part, kdev + (kMaxRestart + 2), stream);
-        launch_axpy_multi(w, V, stride, j + 1, kdev + (kMaxRestart + 2), -1.0, len, stream);
-        launch_dot(w, w, len, part, kdev + 2 * (kMaxRestart + 2), stream);
-        CK(cudaMemcpyAsync(hbuf, kdev, sizeof(double) * (2 * (kMaxRestart + 2) + 1),
-                           cudaMemcpyDeviceToHost, stream));
+        arnoldi_step(o, j, stride, len, tri);
         sync();
         ++total;
         double* h = &H[(size_t)j * (m + 1)];
@@ -514,7 +669,6 @@ struct ipm_solver {
         double hn = std::sqrt(hbuf[2 * (kMaxRestart + 2)]);
         h[j + 1] = hn;
         if (!std::isfinite(hn)) throw IpmError{IPM_EBREAKDOWN, "non-finite Krylov vector"};
-        if (hn > 0.0) launch_axpby(w, w, 1.0 / hn, 0.0, len, stream);
         for (int i = 0; i < j; ++i) {
           double t = cs[i] * h[i] + sn[i] * h[i + 1];
           h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
@@ -652,7 +806,14 @@ struct ipm_solver {
     hist.insert(hist.end(), row, row + kHistCols);
   }
 
+  void apply_flags(const ipm_options& o) {
+    fused = (o.kernel_flags & 1) == 0;
+    nu_fits = o.smooth_pre <= 8 && o.smooth_post <= 8;
+    use_graphs = (o.kernel_flags & 2) == 0;
+  }
+
   int solve(const ipm_options& o, ipm_report* rep) {
+    apply_flags(o);
     if (!has_data) throw IpmError{IPM_ESTATE, "ipm_set_data must precede ipm_solve"};
     if (o.restart < 1 || o.restart > kMaxRestart) throw IpmError{IPM_EINVAL, "restart out of range [1, 100]"};
     if (o.cheb_steps < 1 || o.vcycles < 1 || o.smooth_pre < 0 || o.smooth_post < 0 ||
@@ -663,6 +824,7 @@ struct ipm_solver {
       throw IpmError{IPM_EINVAL, "MINRES needs a symmetric V-cycle (smooth_pre == smooth_post)"};
     auto t0 = std::chrono::steady_clock::now();
     ensure_krylov(o);
+    last_precision = o.precision;
     hist.clear();
     double mu = o.mu0;
     launch_init_state(g, bounds(), st, mu, stream);
@@ -781,6 +943,7 @@ void ipm_default_options(ipm_options* o) {
   o->time_limit_s = 0.0;
   o->common_step = 0;
   o->mu_rule = 0;
+  o->kernel_flags = 0;
 }
 
 int ipm_create(const ipm_grid* grid, const ipm_pde* pde, double alpha, double beta,
@@ -898,10 +1061,14 @@ int ipm_profile_read(ipm_solver* s, double* total_ms, long long* launches, doubl
     s->prof_flush();
     if (total_ms) *total_ms = s->prof_ms;
     if (launches) *launches = s->prof_count;
-    // algorithmic bytes of one finest-level Jacobi sweep: read x, b, m, jinv; write x
+    // algorithmic bytes of one sampled finest-level launch, per unknown: fused 2D kernel
+    // (nu sweeps + residual + restriction) reads x, b, m and writes x and a quarter-size
+    // coarse right-hand side (4.25 values); a single sweep reads x, b, m, jinv and writes x (5)
     long long m = s->g.n - 2;
     long long unknowns = s->g.dim == 3 ? m * m * m : m * m;
-    if (bytes_per_launch) *bytes_per_launch = 5.0 * (double)unknowns * 4.0;
+    double vals = s->fused_mg() ? 4.25 : 5.0;
+    double word = s->last_precision == IPM_PREC_MIXED ? 4.0 : 8.0;
+    if (bytes_per_launch) *bytes_per_launch = vals * (double)unknowns * word;
     return IPM_OK;
   });
 }
@@ -944,6 +1111,7 @@ int ipm_precond_apply_device(ipm_solver* s, const ipm_options* opt, int tri, con
   if (opt) o = *opt;
   else ipm_default_options(&o);
   return guarded(s, [&] {
+    s->apply_flags(o);
     long long f = s->F(), m = s->nn();
     load_diags(s, ty, tw, tv);
     s->setup_precond(o);
@@ -974,6 +1142,7 @@ int ipm_vcycle_device(ipm_solver* s, const ipm_options* opt, int tr, const doubl
   if (opt) o = *opt;
   else ipm_default_options(&o);
   return guarded(s, [&] {
+    s->apply_flags(o);
     launch_pack(s->g, m, s->dg.mh, 1, s->stream);
     s->mg_setup(s->mg64, s->dg.mh);
     launch_pack(s->g, b, s->mg64.lv[0].b, 1, s->stream);
@@ -991,6 +1160,7 @@ int ipm_newton_step_device(ipm_solver* s, const ipm_options* opt, const double* 
   if (opt) o = *opt;
   else ipm_default_options(&o);
   return guarded(s, [&] {
+    s->apply_flags(o);
     if (!s->has_data) throw IpmError{IPM_ESTATE, "ipm_set_data must come first"};
     double* dst[10] = {s->st.y, s->st.w, s->st.v, s->st.p, s->st.lya,
                        s->st.lyb, s->st.lwa, s->st.lwb, s->st.lva, s->st.lvb};

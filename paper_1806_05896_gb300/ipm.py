@@ -58,7 +58,7 @@ class Options(C.Structure):
                 ("cheb_steps", C.c_int), ("vcycles", C.c_int), ("smooth_pre", C.c_int),
                 ("smooth_post", C.c_int), ("max_ipm", C.c_int), ("max_krylov", C.c_int),
                 ("restart", C.c_int), ("fixed_iters", C.c_int), ("time_limit_s", C.c_double),
-                ("common_step", C.c_int), ("mu_rule", C.c_int)]
+                ("common_step", C.c_int), ("mu_rule", C.c_int), ("kernel_flags", C.c_int)]
 
 
 class Report(C.Structure):

@@ -40,12 +40,13 @@ def _iters_to(wl, tol, common=False):
     return len(r.history) - 1
 
 
-@pytest.mark.parametrize("krylov", [ipm.KRYLOV_MINRES_PD, ipm.KRYLOV_GMRES_PT])
-def test_poisson_33_fp64(krylov):
+@pytest.mark.parametrize("krylov,flags", [(ipm.KRYLOV_MINRES_PD, 0), (ipm.KRYLOV_GMRES_PT, 0),
+                                          (ipm.KRYLOV_GMRES_PT, 3)])
+def test_poisson_33_fp64(krylov, flags):
     """The 33^2 Poisson configuration (alpha 1e-2, beta 1e-3, u in [-2, 2]) driven to kkt_rel 1e-10."""
     wl = W.workload_c1()
     k = _iters_to(wl, 1e-10)
-    got, want, rep, hist, ref = _run_pair(wl, k, krylov=krylov)
+    got, want, rep, hist, ref = _run_pair(wl, k, krylov=krylov, kernel_flags=flags)
     for f in ("y", "u", "p"):
         assert rel(got[f], want[f]) < 1e-8, (f, rel(got[f], want[f]))
     assert rep["ipm_iters"] == k and rep["krylov_relres_max"] < 1.5e-10
@@ -95,9 +96,9 @@ def test_gaussian_state_bound_65_blocked_path():
     s.close()
 
 
-@pytest.mark.parametrize("cell", [1, 4, 6])
-def test_mixed_precision_gaussian_65(cell):
-    wl = W.workload_c2(n=65, cell=cell)
+@pytest.mark.parametrize("cell,n", [(1, 65), (4, 65), (6, 65), (1, 129)])
+def test_mixed_precision_gaussian(cell, n):
+    wl = W.workload_c2(n=n, cell=cell)
     k = _iters_to(wl, 1e-6, True)
     got, want, rep, _, _ = _run_pair(wl, k, True, precision=ipm.PREC_MIXED)
     for f in ("y", "u", "p"):
