@@ -182,7 +182,7 @@ IPM_D void cta_sweep(const T* cur, T* nxt, const T* sb, const T* sm, int n, T om
 template <typename T>
 __global__ void __launch_bounds__(1024) k_mg2_coarse(MGCoarse<T> cl, const T* __restrict__ btop,
                                                      T* __restrict__ xtop, T omega, int nu_pre,
-                                                     int nu_post) {
+                                                     int nu_post, int load_x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* base = reinterpret_cast<T*>(smem_raw);
   T* X0[kMaxCoarse];
@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(1024) k_mg2_coarse(MGCoarse<T> cl, const T* __
       int ix = 1 + t % mI, iy = 1 + t / mI;
       Mm[l][iy * n + ix] = cl.m[l][(long long)iy * cl.pitch[l] + ix];
       if (l == 0) B[0][iy * n + ix] = btop[(long long)iy * cl.pitch[0] + ix];
+      if (l == 0 && load_x) X0[0][iy * n + ix] = xtop[(long long)iy * cl.pitch[0] + ix];
     }
   }
   __syncthreads();
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(1024) k_mg2_coarse(MGCoarse<T> cl, const T* __
     for (int s = 0; s < nu_pre; ++s) {
       T* c = cur[l] ? X1[l] : X0[l];
       T* nx = cur[l] ? X0[l] : X1[l];
-      cta_sweep(c, nx, B[l], Mm[l], n, omega, s == 0);
+      cta_sweep(c, nx, B[l], Mm[l], n, omega, s == 0 && !(l == 0 && load_x));
       cur[l] ^= 1;
       __syncthreads();
     }
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(1024) k_mg2_coarse(MGCoarse<T> cl, const T* __
     int n = cl.n[l], nc = cl.n[l + 1], mI = n - 2;
     T* c = cur[l] ? X1[l] : X0[l];
     const T* xcs = cur[l + 1] ? X1[l + 1] : X0[l + 1];
-    if (nu_pre == 0) {  // x was never written on this level in this cycle
+    if (nu_pre == 0 && !(l == 0 && load_x)) {  // x was never written on this level
       for (int t = threadIdx.x; t < mI * mI; t += blockDim.x) c[(1 + t / mI) * n + (1 + t % mI)] = T(0);
       __syncthreads();
     }
@@ -332,12 +333,12 @@ void launch_mg2_prolong_post(const GridDesc& g, const GridDesc& gc, const T* xin
 
 template <typename T>
 void launch_mg2_coarse(const MGCoarse<T>& cl, const T* btop, T* xtop, double omega, int nu_pre,
-                       int nu_post, cudaStream_t s) {
+                       int nu_post, int load_x, cudaStream_t s) {
   static size_t set_to = 0;
   size_t sm = mg2_coarse_smem(cl);
   ensure_smem_attr((const void*)k_mg2_coarse<T>, sm, set_to);
   count_launches(1);
-  k_mg2_coarse<T><<<1, 1024, sm, s>>>(cl, btop, xtop, (T)omega, nu_pre, nu_post);
+  k_mg2_coarse<T><<<1, 1024, sm, s>>>(cl, btop, xtop, (T)omega, nu_pre, nu_post, load_x);
 }
 
 #define IPM_MG2_INST(T)                                                                           \
@@ -347,7 +348,7 @@ void launch_mg2_coarse(const MGCoarse<T>& cl, const T* btop, T* xtop, double ome
                                            cudaStream_t);                                         \
   template void launch_mg2_prolong_post<T>(const GridDesc&, const GridDesc&, const T*, const T*, \
                                            T*, const T*, const T*, double, int, cudaStream_t);   \
-  template void launch_mg2_coarse<T>(const MGCoarse<T>&, const T*, T*, double, int, int,          \
+  template void launch_mg2_coarse<T>(const MGCoarse<T>&, const T*, T*, double, int, int, int,     \
                                      cudaStream_t);
 IPM_MG2_INST(float)
 IPM_MG2_INST(double)

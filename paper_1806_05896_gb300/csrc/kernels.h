@@ -131,7 +131,7 @@ void launch_mg2_prolong_post(const GridDesc& g, const GridDesc& gc, const T* xin
                              cudaStream_t s);
 template <typename T>
 void launch_mg2_coarse(const MGCoarse<T>& cl, const T* btop, T* xtop, double omega, int nu_pre,
-                       int nu_post, cudaStream_t s);
+                       int nu_post, int load_x, cudaStream_t s);
 
 // Temporally blocked Chebyshev (2D): `ns` steps per launch with step weights omega[0..ns)
 constexpr int kMaxChebBlock = 8;

@@ -424,8 +424,10 @@ struct ipm_solver {
       cl.pitch[l - lc] = mg.lv[l].g.pitch;
       cl.m[l - lc] = mg.lv[l].m;
     }
+    // the one-CTA cycle starts from zero below the top level; when it is the top
+    // level itself it continues from the current iterate after the first cycle
     launch_mg2_coarse<T>(cl, mg.lv[lc].b, mg.lv[lc].x[mg.cur[lc]], omega(), o.smooth_pre,
-                         o.smooth_post, stream);
+                         o.smooth_post, (lc == 0 && !zero_x) ? 1 : 0, stream);
     for (int l = lc - 1; l >= 0; --l) {
       MGLevel<T>& L = mg.lv[l];
       int& cur = mg.cur[l];
