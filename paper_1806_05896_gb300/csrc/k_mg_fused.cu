@@ -32,22 +32,25 @@ IPM_D T apply_A(const T* cur, int i, int SX, T mm) {
   return (T(3) * xc - box * T(1.0 / 3.0)) + mm * xc;
 }
 
+// nu damped-Jacobi sweeps on the shared tile; sweep s updates the region shrunk by s.
+// Threads form a 32 x (blockDim / 32) grid over the region (no integer division).
 template <typename T>
-IPM_D void tile_sweeps(T*& cur, T*& nxt, const T* sb, const T* sm, int SX, int SY, int X0, int Y0,
-                       int H, int n, int nu, T omega) {
-  const T kd = T(8.0 / 3.0);
+IPM_D void tile_sweeps(T*& cur, T*& nxt, const T* sb, const T* sm, const T* sj, int SX, int SY,
+                       int X0, int Y0, int H, int n, int nu) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
   for (int s = 1; s <= nu; ++s) {
-    const int w = SX - 2 * s, hh = SY - 2 * s;
-    for (int t = threadIdx.x; t < w * hh; t += blockDim.x) {
-      int lx = s + t % w, ly = s + t / w;
-      int i = ly * SX + lx;
-      T v = T(0);
-      if (inside<T>(X0 - H + lx, Y0 - H + ly, n)) {
-        T xc = cur[i];
-        T ax = apply_A(cur, i, SX, sm[i]);
-        v = xc + (omega / (kd + sm[i])) * (sb[i] - ax);
+    for (int ly = s + ty; ly < SY - s; ly += ny) {
+      const int gy = Y0 - H + ly;
+      for (int lx = s + tx; lx < SX - s; lx += 32) {
+        const int i = ly * SX + lx;
+        T v = T(0);
+        if (inside<T>(X0 - H + lx, gy, n)) {
+          T xc = cur[i];
+          T ax = apply_A(cur, i, SX, sm[i]);
+          v = xc + sj[i] * (sb[i] - ax);
+        }
+        nxt[i] = v;
       }
-      nxt[i] = v;
     }
     __syncthreads();
     T* tmp = cur;
@@ -71,30 +74,39 @@ __global__ void __launch_bounds__(512) k_mg2_pre_restrict(GridDesc g, GridDesc g
   T* s1 = s0 + S;
   T* sb = s1 + S;
   T* sm = sb + S;
+  T* sj = sm + S;
   const int X0 = blockIdx.x * FTX, Y0 = blockIdx.y * FTY;
   const int n = g.n, p = g.pitch;
-  for (int t = threadIdx.x; t < S; t += blockDim.x) {
-    int gx = X0 - H + t % SX, gy = Y0 - H + t / SX;
-    bool in = inside<T>(gx, gy, n);
-    long long c = (long long)gy * p + gx;
-    s0[t] = (in && !zero_init) ? xin[c] : T(0);
-    s1[t] = T(0);
-    sb[t] = in ? b[c] : T(0);
-    sm[t] = in ? m[c] : T(0);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
+  for (int ly = ty; ly < SY; ly += ny) {
+    const int gy = Y0 - H + ly;
+    for (int lx = tx; lx < SX; lx += 32) {
+      const int gx = X0 - H + lx, t = ly * SX + lx;
+      bool in = inside<T>(gx, gy, n);
+      long long c = (long long)gy * p + gx;
+      T mm = in ? m[c] : T(0);
+      s0[t] = (in && !zero_init) ? xin[c] : T(0);
+      s1[t] = T(0);
+      sb[t] = in ? b[c] : T(0);
+      sm[t] = mm;
+      sj[t] = omega / (T(8.0 / 3.0) + mm);
+    }
   }
   __syncthreads();
   T* cur = s0;
   T* nxt = s1;
-  tile_sweeps(cur, nxt, sb, sm, SX, SY, X0, Y0, H, n, nu, omega);
+  tile_sweeps(cur, nxt, sb, sm, sj, SX, SY, X0, Y0, H, n, nu);
   // residual r = b - A x on the tile + halo 1 (into nxt)
   {
-    const int lo = nu + 1, w = SX - 2 * lo, hh = SY - 2 * lo;
-    for (int t = threadIdx.x; t < w * hh; t += blockDim.x) {
-      int lx = lo + t % w, ly = lo + t / w;
-      int i = ly * SX + lx;
-      T r = T(0);
-      if (inside<T>(X0 - H + lx, Y0 - H + ly, n)) r = sb[i] - apply_A(cur, i, SX, sm[i]);
-      nxt[i] = r;
+    const int lo = nu + 1;
+    for (int ly = lo + ty; ly < SY - lo; ly += ny) {
+      const int gy = Y0 - H + ly;
+      for (int lx = lo + tx; lx < SX - lo; lx += 32) {
+        const int i = ly * SX + lx;
+        T r = T(0);
+        if (inside<T>(X0 - H + lx, gy, n)) r = sb[i] - apply_A(cur, i, SX, sm[i]);
+        nxt[i] = r;
+      }
     }
   }
   __syncthreads();
@@ -142,21 +154,28 @@ __global__ void __launch_bounds__(512) k_mg2_prolong_post(GridDesc g, GridDesc g
   T* s1 = s0 + S;
   T* sb = s1 + S;
   T* sm = sb + S;
+  T* sj = sm + S;
   const int X0 = blockIdx.x * FTX, Y0 = blockIdx.y * FTY;
   const int n = g.n, p = g.pitch;
-  for (int t = threadIdx.x; t < S; t += blockDim.x) {
-    int gx = X0 - H + t % SX, gy = Y0 - H + t / SX;
-    bool in = inside<T>(gx, gy, n);
-    long long c = (long long)gy * p + gx;
-    s0[t] = in ? xin[c] + prolong_at(xc, gc.pitch, gx, gy) : T(0);
-    s1[t] = T(0);
-    sb[t] = in ? b[c] : T(0);
-    sm[t] = in ? m[c] : T(0);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
+  for (int ly = ty; ly < SY; ly += ny) {
+    const int gy = Y0 - H + ly;
+    for (int lx = tx; lx < SX; lx += 32) {
+      const int gx = X0 - H + lx, t = ly * SX + lx;
+      bool in = inside<T>(gx, gy, n);
+      long long c = (long long)gy * p + gx;
+      T mm = in ? m[c] : T(0);
+      s0[t] = in ? xin[c] + prolong_at(xc, gc.pitch, gx, gy) : T(0);
+      s1[t] = T(0);
+      sb[t] = in ? b[c] : T(0);
+      sm[t] = mm;
+      sj[t] = omega / (T(8.0 / 3.0) + mm);
+    }
   }
   __syncthreads();
   T* cur = s0;
   T* nxt = s1;
-  tile_sweeps(cur, nxt, sb, sm, SX, SY, X0, Y0, H, n, nu, omega);
+  tile_sweeps(cur, nxt, sb, sm, sj, SX, SY, X0, Y0, H, n, nu);
   for (int t = threadIdx.x; t < FTX * FTY; t += blockDim.x) {
     int gx = X0 + t % FTX, gy = Y0 + t / FTX;
     if (!inside<T>(gx, gy, n)) continue;
@@ -287,7 +306,7 @@ __global__ void __launch_bounds__(1024) k_mg2_coarse(MGCoarse<T> cl, const T* __
 
 template <typename T>
 size_t tile_smem(int halo) {
-  return 4 * (size_t)(FTX + 2 * halo) * (FTY + 2 * halo) * sizeof(T);
+  return 5 * (size_t)(FTX + 2 * halo) * (FTY + 2 * halo) * sizeof(T);
 }
 
 // raise a kernel's dynamic shared memory limit when a launch needs more than the default
@@ -374,48 +393,55 @@ __global__ void __launch_bounds__(512) k_cheb2_block(GridDesc g, ChebSteps cs, c
   T* sc = sbuf + S;
   T* sb = sc + S;
   T* st = sb + S;
+  T* sinv = st + S;  // 1 / (D_M + Theta_y)
   const int X0 = blockIdx.x * FTX, Y0 = blockIdx.y * FTY;
   const int n = g.n, p = g.pitch;
   const T dM = (T)cs.dM, gam = (T)cs.gamma, ms = (T)cs.mscale;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
   T* prev = sa;
   T* cur = sbuf;
   T* nxt = sc;
-  for (int t = threadIdx.x; t < S; t += blockDim.x) {
-    int gx = X0 - H + t % SX, gy = Y0 - H + t / SX;
-    bool in = inside<T>(gx, gy, n);
-    long long c = (long long)gy * p + gx;
-    T bb = in ? (T)b[c] : T(0);
-    T th = in ? thy[c] : T(0);
-    sb[t] = bb;
-    st[t] = th;
-    if (first) {
-      prev[t] = T(0);
-      cur[t] = in ? gam * bb / (dM + th) : T(0);
-    } else {
-      prev[t] = in ? xp_in[c] : T(0);
-      cur[t] = in ? xc_in[c] : T(0);
+  for (int ly = ty; ly < SY; ly += ny) {
+    const int gy = Y0 - H + ly;
+    for (int lx = tx; lx < SX; lx += 32) {
+      const int gx = X0 - H + lx, t = ly * SX + lx;
+      bool in = inside<T>(gx, gy, n);
+      long long c = (long long)gy * p + gx;
+      T bb = in ? (T)b[c] : T(0);
+      T th = in ? thy[c] : T(0);
+      T iv = T(1) / (dM + th);
+      sb[t] = bb;
+      st[t] = th;
+      sinv[t] = iv;
+      if (first) {
+        prev[t] = T(0);
+        cur[t] = in ? gam * bb * iv : T(0);
+      } else {
+        prev[t] = in ? xp_in[c] : T(0);
+        cur[t] = in ? xc_in[c] : T(0);
+      }
+      nxt[t] = T(0);
     }
-    nxt[t] = T(0);
   }
   __syncthreads();
   for (int s = 1; s <= cs.ns; ++s) {
     const T om = (T)cs.omega[s - 1];
-    const int w = SX - 2 * s, hh = SY - 2 * s;
-    for (int t = threadIdx.x; t < w * hh; t += blockDim.x) {
-      int lx = s + t % w, ly = s + t / w;
-      int i = ly * SX + lx;
-      T v = T(0);
-      if (inside<T>(X0 - H + lx, Y0 - H + ly, n)) {
-        T x = cur[i];
-        T r0 = cur[i - SX - 1] + T(4) * cur[i - SX] + cur[i - SX + 1];
-        T r1 = cur[i - 1] + T(4) * x + cur[i + 1];
-        T r2 = cur[i + SX - 1] + T(4) * cur[i + SX] + cur[i + SX + 1];
-        T th = st[i];
-        T ax = ms * (r0 + T(4) * r1 + r2) + th * x;
-        T res = sb[i] - ax;
-        v = x + (om - T(1)) * (x - prev[i]) + om * gam * res / (dM + th);
+    const T og = om * gam;
+    for (int ly = s + ty; ly < SY - s; ly += ny) {
+      const int gy = Y0 - H + ly;
+      for (int lx = s + tx; lx < SX - s; lx += 32) {
+        const int i = ly * SX + lx;
+        T v = T(0);
+        if (inside<T>(X0 - H + lx, gy, n)) {
+          T x = cur[i];
+          T r0 = cur[i - SX - 1] + T(4) * cur[i - SX] + cur[i - SX + 1];
+          T r1 = cur[i - 1] + T(4) * x + cur[i + 1];
+          T r2 = cur[i + SX - 1] + T(4) * cur[i + SX] + cur[i + SX + 1];
+          T ax = ms * (r0 + T(4) * r1 + r2) + st[i] * x;
+          v = x + (om - T(1)) * (x - prev[i]) + og * (sb[i] - ax) * sinv[i];
+        }
+        nxt[i] = v;
       }
-      nxt[i] = v;
     }
     __syncthreads();
     T* tmp = prev;
@@ -444,7 +470,7 @@ void launch_cheb2_block(const GridDesc& g, const ChebSteps& cs, const Ti* b, con
                         const T* xc_in, const T* xp_in, T* xc_out, T* xp_out, To* final_out,
                         int first, cudaStream_t s) {
   static size_t set_to = 0;
-  size_t sm = 5 * (size_t)(FTX + 2 * cs.ns) * (FTY + 2 * cs.ns) * sizeof(T);
+  size_t sm = 6 * (size_t)(FTX + 2 * cs.ns) * (FTY + 2 * cs.ns) * sizeof(T);
   ensure_smem_attr((const void*)k_cheb2_block<T, Ti, To>, sm, set_to);
   dim3 grid((g.n + FTX - 1) / FTX, (g.n + FTY - 1) / FTY);
   count_launches(1);

@@ -395,7 +395,9 @@ struct ipm_solver {
   // first level handled by the one-CTA coarse kernel (2D Poisson fused path)
   template <typename T>
   int coarse_start(const MGHier<T>& mg) const {
-    const int limit = sizeof(T) == 4 ? 65 : 33;
+    // FP32: levels up to 65^2 in one CTA. FP64 runs at 1/64 of the FP32 rate on this
+    // GPU, so one SM is slow: only the last three levels go into the one-CTA kernel.
+    const int limit = sizeof(T) == 4 ? 65 : 9;
     for (int l = 0; l < mg.nlev; ++l)
       if (mg.lv[l].g.n <= limit) return l;
     return mg.nlev - 1;
