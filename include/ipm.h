@@ -164,6 +164,15 @@ long long ipm_launch_count(void);
  * once per unknown, in the precision of the mixed path: 4-byte values). */
 int ipm_profile_smoother(ipm_solver* s, int enable, int every);
 int ipm_profile_read(ipm_solver* s, double* total_ms, long long* launches, double* bytes_per_launch);
+/* Per-stage CUDA-event timing of the Krylov iteration (disables graph replay while on).
+ * Copies the accumulated milliseconds and counts of up to `nphases` stages into ms /
+ * counts (stages: 1 Chebyshev, 2 z-block + coupling, 3 multigrid solves, 4 (M + Theta_y)
+ * product and conversion, 5 normalisation and norm, 6 Newton operator, 7 Gram-Schmidt
+ * dot products, 8 Gram-Schmidt updates; inside the 2D multigrid: 9 finest-level pre-smoothing
+ * + restriction, 10 finest-level prolongation + post-smoothing, 11 the other tiled levels,
+ * 12 the one-CTA coarse cycle), then, if enable >= 0, resets them and switches
+ * stage timing on (1) or off (0). */
+int ipm_profile_phases(ipm_solver* s, int enable, double* ms, long long* counts, int nphases);
 const char* ipm_strerror(int code);
 const char* ipm_last_error(const ipm_solver* s);
 

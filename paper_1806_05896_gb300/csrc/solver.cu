@@ -74,14 +74,19 @@ struct ipm_solver {
   double* hbuf = nullptr;  // pinned
   double* dense = nullptr; // n^d scratch for packing
 
-  // sampled CUDA-event timing of the finest-level smoother launches
+  // sampled CUDA-event timing of the finest-level smoother launches (phase 0), and
+  // with phase timing on, of every stage of the Krylov iteration (phases 1..)
   bool prof_on = false;
+  bool phases_on = false;
   int prof_every = 8;
   long long prof_seen = 0;
   std::vector<cudaEvent_t> prof_ev;
+  std::vector<int> prof_tag;
   int prof_used = 0;
   double prof_ms = 0.0;
   long long prof_count = 0;
+  double ph_ms[16] = {};
+  long long ph_count[16] = {};
 
   double c0 = 0, ncy = 0, nf = 0, nd = 0, nbounds = 0;
   double mean_prod = 0;  // mean complementarity product of the current iterate
@@ -125,22 +130,47 @@ struct ipm_solver {
     for (int i = 0; i + 1 < prof_used; i += 2) {
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, prof_ev[i], prof_ev[i + 1]));
-      prof_ms += ms;
-      ++prof_count;
+      int tag = prof_tag[i / 2];
+      if (tag == 0) {
+        prof_ms += ms;
+        ++prof_count;
+      } else {
+        ph_ms[tag] += ms;
+        ++ph_count[tag];
+      }
     }
     prof_used = 0;
   }
-  // record an event pair around the next launch if this one is sampled
-  bool prof_begin() {
-    if (!prof_on || (prof_seen++ % prof_every) != 0) return false;
-    if (prof_used + 2 > (int)prof_ev.size()) prof_flush();
+  void ensure_events() {
     if (prof_ev.size() < 512) {
       while (prof_ev.size() < 512) {
         cudaEvent_t e;
         CK(cudaEventCreate(&e));
         prof_ev.push_back(e);
       }
+      prof_tag.assign(256, 0);
     }
+  }
+  // phase timing: event pair around a stage (no-op unless phase timing is on)
+  bool ph_begin(int tag) {
+    if (!phases_on) return false;
+    ensure_events();
+    if (prof_used + 2 > (int)prof_ev.size()) prof_flush();
+    prof_tag[prof_used / 2] = tag;
+    CK(cudaEventRecord(prof_ev[prof_used], stream));
+    return true;
+  }
+  void ph_end(bool on) {
+    if (!on) return;
+    CK(cudaEventRecord(prof_ev[prof_used + 1], stream));
+    prof_used += 2;
+  }
+  // record an event pair around the next launch if this one is sampled
+  bool prof_begin() {
+    if (!prof_on || phases_on || (prof_seen++ % prof_every) != 0) return false;
+    ensure_events();
+    if (prof_used + 2 > (int)prof_ev.size()) prof_flush();
+    prof_tag[prof_used / 2] = 0;
     CK(cudaEventRecord(prof_ev[prof_used], stream));
     return true;
   }
@@ -413,9 +443,11 @@ struct ipm_solver {
       MGLevel<T>& L = mg.lv[l];
       int& cur = mg.cur[l];
       bool pr = l == 0 && !(zero_x && l == 0) && prof_begin();
+      bool ph = ph_begin(l == 0 ? 9 : 11);
       launch_mg2_pre_restrict<T>(L.g, mg.lv[l + 1].g, L.x[cur], L.x[1 - cur], L.b, L.m,
                                  mg.lv[l + 1].b, omega(), o.smooth_pre, (l > 0 || zero_x) ? 1 : 0,
                                  stream);
+      ph_end(ph);
       prof_end(pr);
       cur = 1 - cur;
     }
@@ -428,13 +460,17 @@ struct ipm_solver {
     }
     // the one-CTA cycle starts from zero below the top level; when it is the top
     // level itself it continues from the current iterate after the first cycle
+    bool phc = ph_begin(12);
     launch_mg2_coarse<T>(cl, mg.lv[lc].b, mg.lv[lc].x[mg.cur[lc]], omega(), o.smooth_pre,
                          o.smooth_post, (lc == 0 && !zero_x) ? 1 : 0, stream);
+    ph_end(phc);
     for (int l = lc - 1; l >= 0; --l) {
       MGLevel<T>& L = mg.lv[l];
       int& cur = mg.cur[l];
+      bool ph = ph_begin(l == 0 ? 10 : 11);
       launch_mg2_prolong_post<T>(L.g, mg.lv[l + 1].g, L.x[cur], mg.lv[l + 1].x[mg.cur[l + 1]],
                                  L.x[1 - cur], L.b, L.m, omega(), o.smooth_post, stream);
+      ph_end(ph);
       cur = 1 - cur;
     }
   }
@@ -517,22 +553,42 @@ struct ipm_solver {
   void precond(const double* r, double* z, int tri, const ipm_options& o) {
     long long f = F();
     bool mixed = o.precision == IPM_PREC_MIXED;
+    bool p1 = ph_begin(1);
     if (mixed) cheb_apply<float, double>(r, dg.thy32, z, o.cheb_steps, cheb32);
     else cheb_apply<double, double>(r, dg.thy, z, o.cheb_steps, cheb64);
+    ph_end(p1);
+    bool p2 = ph_begin(2);
     launch_zblock(g, alpha * mass_diag(g), r + f, r + 2 * f, dg.thw, dg.thv, z + f, z + 2 * f,
                   stream);
+    if (mixed) launch_coupling<float>(g, opL(), z, z + f, z + 2 * f, r + 3 * f, tri, mg32.lv[0].b, stream);
+    else launch_coupling<double>(g, opL(), z, z + f, z + 2 * f, r + 3 * f, tri, mg64.lv[0].b, stream);
+    ph_end(p2);
     if (mixed) {
-      launch_coupling<float>(g, opL(), z, z + f, z + 2 * f, r + 3 * f, tri, mg32.lv[0].b, stream);
+      bool p3 = ph_begin(3);
       float* s1 = mg_solve(mg32, 0, o);
+      ph_end(p3);
+      bool p4 = ph_begin(4);
       launch_mass_theta<float>(g, s1, dg.thy32, mg32.lv[0].b, stream);
+      ph_end(p4);
+      bool p5 = ph_begin(3);
       float* xp = mg_solve(mg32, 1, o);
+      ph_end(p5);
+      bool p6 = ph_begin(4);
       launch_convert<float, double>(g, xp, z + 3 * f, stream);
+      ph_end(p6);
     } else {
-      launch_coupling<double>(g, opL(), z, z + f, z + 2 * f, r + 3 * f, tri, mg64.lv[0].b, stream);
+      bool p3 = ph_begin(3);
       double* s1 = mg_solve(mg64, 0, o);
+      ph_end(p3);
+      bool p4 = ph_begin(4);
       launch_mass_theta<double>(g, s1, dg.thy, mg64.lv[0].b, stream);
+      ph_end(p4);
+      bool p5 = ph_begin(3);
       double* xp = mg_solve(mg64, 1, o);
+      ph_end(p5);
+      bool p6 = ph_begin(4);
       launch_convert<double, double>(g, xp, z + 3 * f, stream);
+      ph_end(p6);
     }
   }
 
@@ -574,14 +630,28 @@ struct ipm_solver {
     double* zj = Z + (long long)j * stride;
     double* w = V + (long long)(j + 1) * stride;
     const int K = kMaxRestart + 2;
+    bool p0 = ph_begin(5);
     if (j > 0) launch_scale_rsqrt(vj, vj, kdev + 2 * K, len, stream);
+    ph_end(p0);
     precond(vj, zj, tri, o);
+    bool p1 = ph_begin(6);
     newton_apply(zj, w);
+    ph_end(p1);
+    bool p2 = ph_begin(7);
     launch_multidot(V, stride, j + 1, w, len, part, kdev, stream);
+    ph_end(p2);
+    bool p3 = ph_begin(8);
     launch_axpy_multi(w, V, stride, j + 1, kdev, -1.0, len, stream);
+    ph_end(p3);
+    bool p4 = ph_begin(7);
     launch_multidot(V, stride, j + 1, w, len, part, kdev + K, stream);
+    ph_end(p4);
+    bool p5 = ph_begin(8);
     launch_axpy_multi(w, V, stride, j + 1, kdev + K, -1.0, len, stream);
+    ph_end(p5);
+    bool p6 = ph_begin(5);
     launch_dot(w, w, len, part, kdev + 2 * K, stream);
+    ph_end(p6);
     CK(cudaMemcpyAsync(hbuf, kdev, sizeof(double) * (2 * K + 1), cudaMemcpyDeviceToHost, stream));
   }
 
@@ -590,7 +660,7 @@ struct ipm_solver {
                     ((long long)o.cheb_steps << 30) ^ ((long long)o.vcycles << 24) ^
                     ((long long)o.smooth_pre << 16) ^ ((long long)o.smooth_post << 8) ^
                     ((long long)(fused ? 1 : 0) << 4) ^ (long long)(size_t)stream;
-    bool graphs = use_graphs && !prof_on;
+    bool graphs = use_graphs && !prof_on && !phases_on;
     if (!graphs) {
       arnoldi_body(o, j, stride, len, tri);
       return;
@@ -1055,6 +1125,25 @@ int ipm_profile_smoother(ipm_solver* s, int enable, int every) {
     s->prof_seen = 0;
     s->prof_ms = 0.0;
     s->prof_count = 0;
+    return IPM_OK;
+  });
+}
+
+int ipm_profile_phases(ipm_solver* s, int enable, double* ms, long long* counts, int nphases) {
+  if (!s) return IPM_EINVAL;
+  return guarded(s, [&] {
+    s->prof_flush();
+    for (int i = 0; i < nphases && i < 16; ++i) {
+      if (ms) ms[i] = s->ph_ms[i];
+      if (counts) counts[i] = s->ph_count[i];
+    }
+    if (enable >= 0) {
+      s->phases_on = enable != 0;
+      for (int i = 0; i < 16; ++i) {
+        s->ph_ms[i] = 0.0;
+        s->ph_count[i] = 0;
+      }
+    }
     return IPM_OK;
   });
 }

@@ -30,7 +30,7 @@ EXPORTED = (
     "ipm_set_data_device", "ipm_solve", "ipm_get_state", "ipm_get_control", "ipm_get_adjoint",
     "ipm_get_state_device", "ipm_get_control_device", "ipm_get_adjoint_device",
     "ipm_get_history", "ipm_destroy", "ipm_launch_count",
-    "ipm_profile_smoother", "ipm_profile_read", "ipm_strerror", "ipm_last_error",
+    "ipm_profile_smoother", "ipm_profile_read", "ipm_profile_phases", "ipm_strerror", "ipm_last_error",
     "ipm_newton_apply_device", "ipm_precond_apply_device", "ipm_chebyshev_device",
     "ipm_vcycle_device", "ipm_newton_step_device", "ipm_chebyshev_noalloc",
 )
@@ -106,6 +106,7 @@ def load() -> C.CDLL:
     lib.ipm_launch_count.restype = C.c_longlong
     lib.ipm_profile_smoother.argtypes = [P, C.c_int, C.c_int]
     lib.ipm_profile_read.argtypes = [P, D, C.POINTER(C.c_longlong), D]
+    lib.ipm_profile_phases.argtypes = [P, C.c_int, D, C.POINTER(C.c_longlong), C.c_int]
     lib.ipm_strerror.argtypes = [C.c_int]
     lib.ipm_strerror.restype = C.c_char_p
     lib.ipm_last_error.argtypes = [P]
@@ -262,6 +263,17 @@ class Solver:
         by = C.c_double()
         self._check(self._lib.ipm_profile_read(self._h, C.byref(ms), C.byref(cnt), C.byref(by)))
         return ms.value, cnt.value, by.value
+
+    PHASES = ("", "chebyshev", "zblock+coupling", "multigrid", "mass_theta+convert",
+              "normalise+norm", "newton_operator", "gs_dots", "gs_updates", "mg_fine_pre",
+              "mg_fine_post", "mg_mid_levels", "mg_coarse_cta")
+
+    def profile_phases(self, enable: int):
+        """Return accumulated per-stage (ms, count) and reset; enable: 1 on, 0 off, -1 keep."""
+        ms = (C.c_double * 16)()
+        cnt = (C.c_longlong * 16)()
+        self._check(self._lib.ipm_profile_phases(self._h, enable, ms, cnt, 16))
+        return {nm: (ms[i], cnt[i]) for i, nm in enumerate(self.PHASES) if nm}
 
     def history(self) -> list:
         nr = C.c_int()
