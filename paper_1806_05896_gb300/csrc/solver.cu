@@ -142,43 +142,49 @@ struct ipm_solver {
     prof_used = 0;
   }
   void ensure_events() {
-    if (prof_ev.size() < 512) {
-      while (prof_ev.size() < 512) {
+    if (prof_ev.size() < 8192) {
+      while (prof_ev.size() < 8192) {
         cudaEvent_t e;
         CK(cudaEventCreate(&e));
         prof_ev.push_back(e);
       }
-      prof_tag.assign(256, 0);
+      prof_tag.assign(4096, 0);
     }
   }
-  // phase timing: event pair around a stage (no-op unless phase timing is on)
-  bool ph_begin(int tag) {
-    if (!phases_on) return false;
+  int prof_open = 0;  // event pairs begun but not yet ended
+  // event pair around a stage: the slot is reserved at begin, so stages may nest;
+  // returns -1 when timing is off or the pool is full
+  int ph_begin(int tag) {
+    if (!phases_on) return -1;
     ensure_events();
-    if (prof_used + 2 > (int)prof_ev.size()) prof_flush();
-    prof_tag[prof_used / 2] = tag;
-    CK(cudaEventRecord(prof_ev[prof_used], stream));
-    return true;
-  }
-  void ph_end(bool on) {
-    if (!on) return;
-    CK(cudaEventRecord(prof_ev[prof_used + 1], stream));
+    if (prof_used + 2 > (int)prof_ev.size() && prof_open == 0) prof_flush();
+    if (prof_used + 2 > (int)prof_ev.size()) return -1;
+    int slot = prof_used;
     prof_used += 2;
+    ++prof_open;
+    prof_tag[slot / 2] = tag;
+    CK(cudaEventRecord(prof_ev[slot], stream));
+    return slot;
   }
-  // record an event pair around the next launch if this one is sampled
-  bool prof_begin() {
-    if (!prof_on || phases_on || (prof_seen++ % prof_every) != 0) return false;
+  void ph_end(int slot) {
+    if (slot < 0) return;
+    CK(cudaEventRecord(prof_ev[slot + 1], stream));
+    --prof_open;
+  }
+  // sampled smoother timing (tag 0)
+  int prof_begin() {
+    if (!prof_on || phases_on || (prof_seen++ % prof_every) != 0) return -1;
     ensure_events();
-    if (prof_used + 2 > (int)prof_ev.size()) prof_flush();
-    prof_tag[prof_used / 2] = 0;
-    CK(cudaEventRecord(prof_ev[prof_used], stream));
-    return true;
-  }
-  void prof_end(bool on) {
-    if (!on) return;
-    CK(cudaEventRecord(prof_ev[prof_used + 1], stream));
+    if (prof_used + 2 > (int)prof_ev.size() && prof_open == 0) prof_flush();
+    if (prof_used + 2 > (int)prof_ev.size()) return -1;
+    int slot = prof_used;
     prof_used += 2;
+    ++prof_open;
+    prof_tag[slot / 2] = 0;
+    CK(cudaEventRecord(prof_ev[slot], stream));
+    return slot;
   }
+  void prof_end(int slot) { ph_end(slot); }
 
   void drop_graphs() {
     for (cudaGraphExec_t e : gexec)
@@ -402,7 +408,7 @@ struct ipm_solver {
     }
     bool z = zero_x;
     for (int i = 0; i < o.smooth_pre; ++i) {
-      bool pr = l == 0 && !z && prof_begin();
+      int pr = (l == 0 && !z) ? prof_begin() : -1;
       launch_mg_smooth<T>(L.g, opL(), L.x[cur], L.x[1 - cur], L.b, L.m, L.jinv, z, tr, stream);
       prof_end(pr);
       cur = 1 - cur;
@@ -415,7 +421,7 @@ struct ipm_solver {
     vcycle(mg, l + 1, true, tr, o);
     launch_mg_prolong_add<T>(L.g, C.g, C.x[mg.cur[l + 1]], L.x[cur], stream);
     for (int i = 0; i < o.smooth_post; ++i) {
-      bool pr = l == 0 && prof_begin();
+      int pr = l == 0 ? prof_begin() : -1;
       launch_mg_smooth<T>(L.g, opL(), L.x[cur], L.x[1 - cur], L.b, L.m, L.jinv, 0, tr, stream);
       prof_end(pr);
       cur = 1 - cur;
@@ -442,8 +448,8 @@ struct ipm_solver {
     for (int l = 0; l < lc; ++l) {
       MGLevel<T>& L = mg.lv[l];
       int& cur = mg.cur[l];
-      bool pr = l == 0 && !(zero_x && l == 0) && prof_begin();
-      bool ph = ph_begin(l == 0 ? 9 : 11);
+      int pr = (l == 0 && !zero_x) ? prof_begin() : -1;
+      int ph = ph_begin(l == 0 ? 9 : 11);
       launch_mg2_pre_restrict<T>(L.g, mg.lv[l + 1].g, L.x[cur], L.x[1 - cur], L.b, L.m,
                                  mg.lv[l + 1].b, omega(), o.smooth_pre, (l > 0 || zero_x) ? 1 : 0,
                                  stream);
@@ -460,14 +466,14 @@ struct ipm_solver {
     }
     // the one-CTA cycle starts from zero below the top level; when it is the top
     // level itself it continues from the current iterate after the first cycle
-    bool phc = ph_begin(12);
+    int phc = ph_begin(12);
     launch_mg2_coarse<T>(cl, mg.lv[lc].b, mg.lv[lc].x[mg.cur[lc]], omega(), o.smooth_pre,
                          o.smooth_post, (lc == 0 && !zero_x) ? 1 : 0, stream);
     ph_end(phc);
     for (int l = lc - 1; l >= 0; --l) {
       MGLevel<T>& L = mg.lv[l];
       int& cur = mg.cur[l];
-      bool ph = ph_begin(l == 0 ? 10 : 11);
+      int ph = ph_begin(l == 0 ? 10 : 11);
       launch_mg2_prolong_post<T>(L.g, mg.lv[l + 1].g, L.x[cur], mg.lv[l + 1].x[mg.cur[l + 1]],
                                  L.x[1 - cur], L.b, L.m, omega(), o.smooth_post, stream);
       ph_end(ph);
@@ -553,40 +559,40 @@ struct ipm_solver {
   void precond(const double* r, double* z, int tri, const ipm_options& o) {
     long long f = F();
     bool mixed = o.precision == IPM_PREC_MIXED;
-    bool p1 = ph_begin(1);
+    int p1 = ph_begin(1);
     if (mixed) cheb_apply<float, double>(r, dg.thy32, z, o.cheb_steps, cheb32);
     else cheb_apply<double, double>(r, dg.thy, z, o.cheb_steps, cheb64);
     ph_end(p1);
-    bool p2 = ph_begin(2);
+    int p2 = ph_begin(2);
     launch_zblock(g, alpha * mass_diag(g), r + f, r + 2 * f, dg.thw, dg.thv, z + f, z + 2 * f,
                   stream);
     if (mixed) launch_coupling<float>(g, opL(), z, z + f, z + 2 * f, r + 3 * f, tri, mg32.lv[0].b, stream);
     else launch_coupling<double>(g, opL(), z, z + f, z + 2 * f, r + 3 * f, tri, mg64.lv[0].b, stream);
     ph_end(p2);
     if (mixed) {
-      bool p3 = ph_begin(3);
+      int p3 = ph_begin(3);
       float* s1 = mg_solve(mg32, 0, o);
       ph_end(p3);
-      bool p4 = ph_begin(4);
+      int p4 = ph_begin(4);
       launch_mass_theta<float>(g, s1, dg.thy32, mg32.lv[0].b, stream);
       ph_end(p4);
-      bool p5 = ph_begin(3);
+      int p5 = ph_begin(3);
       float* xp = mg_solve(mg32, 1, o);
       ph_end(p5);
-      bool p6 = ph_begin(4);
+      int p6 = ph_begin(4);
       launch_convert<float, double>(g, xp, z + 3 * f, stream);
       ph_end(p6);
     } else {
-      bool p3 = ph_begin(3);
+      int p3 = ph_begin(3);
       double* s1 = mg_solve(mg64, 0, o);
       ph_end(p3);
-      bool p4 = ph_begin(4);
+      int p4 = ph_begin(4);
       launch_mass_theta<double>(g, s1, dg.thy, mg64.lv[0].b, stream);
       ph_end(p4);
-      bool p5 = ph_begin(3);
+      int p5 = ph_begin(3);
       double* xp = mg_solve(mg64, 1, o);
       ph_end(p5);
-      bool p6 = ph_begin(4);
+      int p6 = ph_begin(4);
       launch_convert<double, double>(g, xp, z + 3 * f, stream);
       ph_end(p6);
     }
@@ -630,26 +636,26 @@ struct ipm_solver {
     double* zj = Z + (long long)j * stride;
     double* w = V + (long long)(j + 1) * stride;
     const int K = kMaxRestart + 2;
-    bool p0 = ph_begin(5);
+    int p0 = ph_begin(5);
     if (j > 0) launch_scale_rsqrt(vj, vj, kdev + 2 * K, len, stream);
     ph_end(p0);
     precond(vj, zj, tri, o);
-    bool p1 = ph_begin(6);
+    int p1 = ph_begin(6);
     newton_apply(zj, w);
     ph_end(p1);
-    bool p2 = ph_begin(7);
+    int p2 = ph_begin(7);
     launch_multidot(V, stride, j + 1, w, len, part, kdev, stream);
     ph_end(p2);
-    bool p3 = ph_begin(8);
+    int p3 = ph_begin(8);
     launch_axpy_multi(w, V, stride, j + 1, kdev, -1.0, len, stream);
     ph_end(p3);
-    bool p4 = ph_begin(7);
+    int p4 = ph_begin(7);
     launch_multidot(V, stride, j + 1, w, len, part, kdev + K, stream);
     ph_end(p4);
-    bool p5 = ph_begin(8);
+    int p5 = ph_begin(8);
     launch_axpy_multi(w, V, stride, j + 1, kdev + K, -1.0, len, stream);
     ph_end(p5);
-    bool p6 = ph_begin(5);
+    int p6 = ph_begin(5);
     launch_dot(w, w, len, part, kdev + 2 * K, stream);
     ph_end(p6);
     CK(cudaMemcpyAsync(hbuf, kdev, sizeof(double) * (2 * K + 1), cudaMemcpyDeviceToHost, stream));
