@@ -104,7 +104,8 @@ typedef struct {
   int common_step; /* 0: separate alpha_P, alpha_D (Algorithm A.1); 1: both = min(alpha_P, alpha_D) */
   int mu_rule;     /* 0: mu <- sigma mu (Algorithm A.1); 1: mu <- sigma * mean complementarity product */
   int kernel_flags; /* 0: fastest kernels; bit 0: per-sweep multigrid/Chebyshev kernels instead of
-                       the fused 2D ones; bit 1: no CUDA-graph replay of Krylov iterations */
+                       the fused 2D ones; bit 1: no CUDA-graph replay of Krylov iterations;
+                       bits 2 / 3: on the mixed path keep the Chebyshev / multigrid stage in FP64 */
 } ipm_options;
 
 typedef struct {

@@ -59,7 +59,7 @@ IPM_D void tile_sweeps(T*& cur, T*& nxt, const T* sb, const T* sm, const T* sj, 
   }
 }
 
-template <typename T>
+template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(512) k_mg2_pre_restrict(GridDesc g, GridDesc gc,
                                                           const T* __restrict__ xin,
                                                           T* __restrict__ xout,
@@ -69,13 +69,13 @@ __global__ void __launch_bounds__(512) k_mg2_pre_restrict(GridDesc g, GridDesc g
                                                           int zero_init) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int H = nu + 2;
-  const int SX = FTX + 2 * H, SY = FTY + 2 * H, S = SX * SY;
+  const int SX = TX + 2 * H, SY = TY + 2 * H, S = SX * SY;
   T* s0 = reinterpret_cast<T*>(smem_raw);
   T* s1 = s0 + S;
   T* sb = s1 + S;
   T* sm = sb + S;
   T* sj = sm + S;
-  const int X0 = blockIdx.x * FTX, Y0 = blockIdx.y * FTY;
+  const int X0 = blockIdx.x * TX, Y0 = blockIdx.y * TY;
   const int n = g.n, p = g.pitch;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
   for (int ly = ty; ly < SY; ly += ny) {
@@ -112,8 +112,8 @@ __global__ void __launch_bounds__(512) k_mg2_pre_restrict(GridDesc g, GridDesc g
   __syncthreads();
   // full-weighting restriction onto the coarse nodes (2I, 2J) inside the tile
   const int nc = gc.n;
-  for (int t = threadIdx.x; t < (FTX / 2) * (FTY / 2); t += blockDim.x) {
-    int I = X0 / 2 + t % (FTX / 2), J = Y0 / 2 + t / (FTX / 2);
+  for (int t = threadIdx.x; t < (TX / 2) * (TY / 2); t += blockDim.x) {
+    int I = X0 / 2 + t % (TX / 2), J = Y0 / 2 + t / (TX / 2);
     if (I < 1 || I > nc - 2 || J < 1 || J > nc - 2) continue;
     int i = (2 * J - Y0 + H) * SX + (2 * I - X0 + H);
     T r0 = T(0.5) * nxt[i - SX - 1] + nxt[i - SX] + T(0.5) * nxt[i - SX + 1];
@@ -121,8 +121,8 @@ __global__ void __launch_bounds__(512) k_mg2_pre_restrict(GridDesc g, GridDesc g
     T r2 = T(0.5) * nxt[i + SX - 1] + nxt[i + SX] + T(0.5) * nxt[i + SX + 1];
     bc[(long long)J * gc.pitch + I] = T(0.5) * r0 + r1 + T(0.5) * r2;
   }
-  for (int t = threadIdx.x; t < FTX * FTY; t += blockDim.x) {
-    int gx = X0 + t % FTX, gy = Y0 + t / FTX;
+  for (int t = threadIdx.x; t < TX * TY; t += blockDim.x) {
+    int gx = X0 + t % TX, gy = Y0 + t / TX;
     if (!inside<T>(gx, gy, n)) continue;
     xout[(long long)gy * p + gx] = cur[(gy - Y0 + H) * SX + (gx - X0 + H)];
   }
@@ -139,7 +139,7 @@ IPM_D T prolong_at(const T* __restrict__ xc, int cp, int i, int j) {
   return wi * wj * T(1) * acc;
 }
 
-template <typename T>
+template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(512) k_mg2_prolong_post(GridDesc g, GridDesc gc,
                                                           const T* __restrict__ xin,
                                                           const T* __restrict__ xc,
@@ -149,13 +149,13 @@ __global__ void __launch_bounds__(512) k_mg2_prolong_post(GridDesc g, GridDesc g
                                                           int nu) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int H = nu;
-  const int SX = FTX + 2 * H, SY = FTY + 2 * H, S = SX * SY;
+  const int SX = TX + 2 * H, SY = TY + 2 * H, S = SX * SY;
   T* s0 = reinterpret_cast<T*>(smem_raw);
   T* s1 = s0 + S;
   T* sb = s1 + S;
   T* sm = sb + S;
   T* sj = sm + S;
-  const int X0 = blockIdx.x * FTX, Y0 = blockIdx.y * FTY;
+  const int X0 = blockIdx.x * TX, Y0 = blockIdx.y * TY;
   const int n = g.n, p = g.pitch;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
   for (int ly = ty; ly < SY; ly += ny) {
@@ -176,8 +176,8 @@ __global__ void __launch_bounds__(512) k_mg2_prolong_post(GridDesc g, GridDesc g
   T* cur = s0;
   T* nxt = s1;
   tile_sweeps(cur, nxt, sb, sm, sj, SX, SY, X0, Y0, H, n, nu);
-  for (int t = threadIdx.x; t < FTX * FTY; t += blockDim.x) {
-    int gx = X0 + t % FTX, gy = Y0 + t / FTX;
+  for (int t = threadIdx.x; t < TX * TY; t += blockDim.x) {
+    int gx = X0 + t % TX, gy = Y0 + t / TX;
     if (!inside<T>(gx, gy, n)) continue;
     xout[(long long)gy * p + gx] = cur[(gy - Y0 + H) * SX + (gx - X0 + H)];
   }
@@ -186,16 +186,17 @@ __global__ void __launch_bounds__(512) k_mg2_prolong_post(GridDesc g, GridDesc g
 // ---------------------------------------------------------------------------
 // One CTA, all coarse levels in shared memory (dense n x n per level).
 // ---------------------------------------------------------------------------
+// one damped-Jacobi sweep over the interior of an n x n level (threads as 32 x 32 grid)
 template <typename T>
-IPM_D void cta_sweep(const T* cur, T* nxt, const T* sb, const T* sm, int n, T omega, int zero) {
-  const T kd = T(8.0 / 3.0);
-  const int m = n - 2;
-  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-    int i = (1 + t / m) * n + (1 + t % m);
-    T xc = zero ? T(0) : cur[i];
-    T ax = zero ? T(0) : apply_A(cur, i, n, sm[i]);
-    nxt[i] = xc + (omega / (kd + sm[i])) * (sb[i] - ax);
-  }
+IPM_D void cta_sweep(const T* cur, T* nxt, const T* sb, const T* sm, const T* sj, int n, int zero) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
+  for (int iy = 1 + ty; iy < n - 1; iy += ny)
+    for (int ix = 1 + tx; ix < n - 1; ix += 32) {
+      const int i = iy * n + ix;
+      T xc = zero ? T(0) : cur[i];
+      T ax = zero ? T(0) : apply_A(cur, i, n, sm[i]);
+      nxt[i] = xc + sj[i] * (sb[i] - ax);
+    }
 }
 
 template <typename T>
@@ -209,6 +210,7 @@ __global__ void __launch_bounds__(1024) k_mg2_coarse(MGCoarse<T> cl, const T* __
   T* B[kMaxCoarse];
   T* R[kMaxCoarse];
   T* Mm[kMaxCoarse];
+  T* Jv[kMaxCoarse];
   int off = 0;
   for (int l = 0; l < cl.nl; ++l) {
     int s = cl.n[l] * cl.n[l];
@@ -217,19 +219,23 @@ __global__ void __launch_bounds__(1024) k_mg2_coarse(MGCoarse<T> cl, const T* __
     B[l] = X1[l] + s;
     R[l] = B[l] + s;
     Mm[l] = R[l] + s;
-    off += 5 * s;
+    Jv[l] = Mm[l] + s;
+    off += 6 * s;
   }
   // zero everything, then load b (top level) and m (all levels), interior entries
   for (int t = threadIdx.x; t < off; t += blockDim.x) base[t] = T(0);
   __syncthreads();
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
   for (int l = 0; l < cl.nl; ++l) {
-    int n = cl.n[l], mI = n - 2;
-    for (int t = threadIdx.x; t < mI * mI; t += blockDim.x) {
-      int ix = 1 + t % mI, iy = 1 + t / mI;
-      Mm[l][iy * n + ix] = cl.m[l][(long long)iy * cl.pitch[l] + ix];
-      if (l == 0) B[0][iy * n + ix] = btop[(long long)iy * cl.pitch[0] + ix];
-      if (l == 0 && load_x) X0[0][iy * n + ix] = xtop[(long long)iy * cl.pitch[0] + ix];
-    }
+    int n = cl.n[l];
+    for (int iy = 1 + ty; iy < n - 1; iy += ny)
+      for (int ix = 1 + tx; ix < n - 1; ix += 32) {
+        T mm = cl.m[l][(long long)iy * cl.pitch[l] + ix];
+        Mm[l][iy * n + ix] = mm;
+        Jv[l][iy * n + ix] = omega / (T(8.0 / 3.0) + mm);
+        if (l == 0) B[0][iy * n + ix] = btop[(long long)iy * cl.pitch[0] + ix];
+        if (l == 0 && load_x) X0[0][iy * n + ix] = xtop[(long long)iy * cl.pitch[0] + ix];
+      }
   }
   __syncthreads();
   int cur[kMaxCoarse];
@@ -240,30 +246,30 @@ __global__ void __launch_bounds__(1024) k_mg2_coarse(MGCoarse<T> cl, const T* __
     for (int s = 0; s < nu_pre; ++s) {
       T* c = cur[l] ? X1[l] : X0[l];
       T* nx = cur[l] ? X0[l] : X1[l];
-      cta_sweep(c, nx, B[l], Mm[l], n, omega, s == 0 && !(l == 0 && load_x));
+      cta_sweep(c, nx, B[l], Mm[l], Jv[l], n, s == 0 && !(l == 0 && load_x));
       cur[l] ^= 1;
       __syncthreads();
     }
     {
       T* c = cur[l] ? X1[l] : X0[l];
-      int mI = n - 2;
-      for (int t = threadIdx.x; t < mI * mI; t += blockDim.x) {
-        int i = (1 + t / mI) * n + (1 + t % mI);
-        R[l][i] = B[l][i] - apply_A(c, i, n, Mm[l][i]);
-      }
+      for (int iy = 1 + ty; iy < n - 1; iy += ny)
+        for (int ix = 1 + tx; ix < n - 1; ix += 32) {
+          const int i = iy * n + ix;
+          R[l][i] = B[l][i] - apply_A(c, i, n, Mm[l][i]);
+        }
     }
     __syncthreads();
     {
-      int nc = cl.n[l + 1], mc = nc - 2;
-      for (int t = threadIdx.x; t < mc * mc; t += blockDim.x) {
-        int I = 1 + t % mc, J = 1 + t / mc;
-        int i = (2 * J) * n + 2 * I;
-        const T* r = R[l];
-        T r0 = T(0.5) * r[i - n - 1] + r[i - n] + T(0.5) * r[i - n + 1];
-        T r1 = T(0.5) * r[i - 1] + r[i] + T(0.5) * r[i + 1];
-        T r2 = T(0.5) * r[i + n - 1] + r[i + n] + T(0.5) * r[i + n + 1];
-        B[l + 1][J * nc + I] = T(0.5) * r0 + r1 + T(0.5) * r2;
-      }
+      int nc = cl.n[l + 1];
+      for (int J = 1 + ty; J < nc - 1; J += ny)
+        for (int I = 1 + tx; I < nc - 1; I += 32) {
+          int i = (2 * J) * n + 2 * I;
+          const T* r = R[l];
+          T r0 = T(0.5) * r[i - n - 1] + r[i - n] + T(0.5) * r[i - n + 1];
+          T r1 = T(0.5) * r[i - 1] + r[i] + T(0.5) * r[i + 1];
+          T r2 = T(0.5) * r[i + n - 1] + r[i + n] + T(0.5) * r[i + n + 1];
+          B[l + 1][J * nc + I] = T(0.5) * r0 + r1 + T(0.5) * r2;
+        }
     }
     __syncthreads();
   }
@@ -274,39 +280,35 @@ __global__ void __launch_bounds__(1024) k_mg2_coarse(MGCoarse<T> cl, const T* __
   }
   __syncthreads();
   for (int l = L - 1; l >= 0; --l) {
-    int n = cl.n[l], nc = cl.n[l + 1], mI = n - 2;
+    int n = cl.n[l], nc = cl.n[l + 1];
     T* c = cur[l] ? X1[l] : X0[l];
     const T* xcs = cur[l + 1] ? X1[l + 1] : X0[l + 1];
-    if (nu_pre == 0 && !(l == 0 && load_x)) {  // x was never written on this level
-      for (int t = threadIdx.x; t < mI * mI; t += blockDim.x) c[(1 + t / mI) * n + (1 + t % mI)] = T(0);
-      __syncthreads();
-    }
-    for (int t = threadIdx.x; t < mI * mI; t += blockDim.x) {
-      int ix = 1 + t % mI, iy = 1 + t / mI;
-      c[iy * n + ix] += prolong_at(xcs, nc, ix, iy);
-    }
+    const bool wipe = nu_pre == 0 && !(l == 0 && load_x);  // x never written on this level
+    for (int iy = 1 + ty; iy < n - 1; iy += ny)
+      for (int ix = 1 + tx; ix < n - 1; ix += 32) {
+        T base_v = wipe ? T(0) : c[iy * n + ix];
+        c[iy * n + ix] = base_v + prolong_at(xcs, nc, ix, iy);
+      }
     __syncthreads();
     for (int s = 0; s < nu_post; ++s) {
       T* cc = cur[l] ? X1[l] : X0[l];
       T* nx = cur[l] ? X0[l] : X1[l];
-      cta_sweep(cc, nx, B[l], Mm[l], n, omega, 0);
+      cta_sweep(cc, nx, B[l], Mm[l], Jv[l], n, 0);
       cur[l] ^= 1;
       __syncthreads();
     }
   }
   {
-    int n = cl.n[0], mI = n - 2;
+    int n = cl.n[0];
     const T* c = cur[0] ? X1[0] : X0[0];
-    for (int t = threadIdx.x; t < mI * mI; t += blockDim.x) {
-      int ix = 1 + t % mI, iy = 1 + t / mI;
-      xtop[(long long)iy * cl.pitch[0] + ix] = c[iy * n + ix];
-    }
+    for (int iy = 1 + ty; iy < n - 1; iy += ny)
+      for (int ix = 1 + tx; ix < n - 1; ix += 32) xtop[(long long)iy * cl.pitch[0] + ix] = c[iy * n + ix];
   }
 }
 
 template <typename T>
-size_t tile_smem(int halo) {
-  return 5 * (size_t)(FTX + 2 * halo) * (FTY + 2 * halo) * sizeof(T);
+size_t tile_smem(int halo, int tx, int ty) {
+  return 5 * (size_t)(tx + 2 * halo) * (ty + 2 * halo) * sizeof(T);
 }
 
 // raise a kernel's dynamic shared memory limit when a launch needs more than the default
@@ -322,32 +324,54 @@ void ensure_smem_attr(const void* fn, size_t bytes, size_t& set_to) {
 template <typename T>
 size_t mg2_coarse_smem(const MGCoarse<T>& cl) {
   size_t s = 0;
-  for (int l = 0; l < cl.nl; ++l) s += 5 * (size_t)cl.n[l] * cl.n[l];
+  for (int l = 0; l < cl.nl; ++l) s += 6 * (size_t)cl.n[l] * cl.n[l];
   return s * sizeof(T);
+}
+
+// large levels: 64 x 32 tiles, 512 threads; smaller levels: 32 x 16 tiles, 256 threads
+// (shorter per-CTA latency and more CTAs in flight where there are few tiles)
+template <typename T, int TX, int TY>
+void pre_restrict_tiles(const GridDesc& g, const GridDesc& gc, const T* xin, T* xout, const T* b,
+                        const T* m, T* bc, double omega, int nu, int zero_init, int threads,
+                        cudaStream_t s) {
+  static size_t set_to = 0;
+  size_t sm = tile_smem<T>(nu + 2, TX, TY);
+  ensure_smem_attr((const void*)k_mg2_pre_restrict<T, TX, TY>, sm, set_to);
+  dim3 grid((g.n + TX - 1) / TX, (g.n + TY - 1) / TY);
+  count_launches(1);
+  k_mg2_pre_restrict<T, TX, TY><<<grid, threads, sm, s>>>(g, gc, xin, xout, b, m, bc, (T)omega, nu,
+                                                          zero_init);
 }
 
 template <typename T>
 void launch_mg2_pre_restrict(const GridDesc& g, const GridDesc& gc, const T* xin, T* xout,
                              const T* b, const T* m, T* bc, double omega, int nu, int zero_init,
                              cudaStream_t s) {
+  if (g.n >= 513)
+    pre_restrict_tiles<T, 64, 32>(g, gc, xin, xout, b, m, bc, omega, nu, zero_init, 512, s);
+  else
+    pre_restrict_tiles<T, 32, 16>(g, gc, xin, xout, b, m, bc, omega, nu, zero_init, 256, s);
+}
+
+template <typename T, int TX, int TY>
+void prolong_post_tiles(const GridDesc& g, const GridDesc& gc, const T* xin, const T* xc, T* xout,
+                        const T* b, const T* m, double omega, int nu, int threads,
+                        cudaStream_t s) {
   static size_t set_to = 0;
-  size_t sm = tile_smem<T>(nu + 2);
-  ensure_smem_attr((const void*)k_mg2_pre_restrict<T>, sm, set_to);
-  dim3 grid((g.n + FTX - 1) / FTX, (g.n + FTY - 1) / FTY);
+  size_t sm = tile_smem<T>(nu, TX, TY);
+  ensure_smem_attr((const void*)k_mg2_prolong_post<T, TX, TY>, sm, set_to);
+  dim3 grid((g.n + TX - 1) / TX, (g.n + TY - 1) / TY);
   count_launches(1);
-  k_mg2_pre_restrict<T><<<grid, 512, sm, s>>>(g, gc, xin, xout, b, m, bc, (T)omega, nu, zero_init);
+  k_mg2_prolong_post<T, TX, TY><<<grid, threads, sm, s>>>(g, gc, xin, xc, xout, b, m, (T)omega,
+                                                          nu);
 }
 
 template <typename T>
 void launch_mg2_prolong_post(const GridDesc& g, const GridDesc& gc, const T* xin, const T* xc,
                              T* xout, const T* b, const T* m, double omega, int nu,
                              cudaStream_t s) {
-  static size_t set_to = 0;
-  size_t sm = tile_smem<T>(nu);
-  ensure_smem_attr((const void*)k_mg2_prolong_post<T>, sm, set_to);
-  dim3 grid((g.n + FTX - 1) / FTX, (g.n + FTY - 1) / FTY);
-  count_launches(1);
-  k_mg2_prolong_post<T><<<grid, 512, sm, s>>>(g, gc, xin, xc, xout, b, m, (T)omega, nu);
+  if (g.n >= 513) prolong_post_tiles<T, 64, 32>(g, gc, xin, xc, xout, b, m, omega, nu, 512, s);
+  else prolong_post_tiles<T, 32, 16>(g, gc, xin, xc, xout, b, m, omega, nu, 256, s);
 }
 
 template <typename T>

@@ -558,9 +558,11 @@ struct ipm_solver {
   // z = P^{-1} r, P = P_T (tri) or P_D (Section 4.2)
   void precond(const double* r, double* z, int tri, const ipm_options& o) {
     long long f = F();
-    bool mixed = o.precision == IPM_PREC_MIXED;
+    // kernel_flags bits 2 / 3 keep the Chebyshev / multigrid stage in FP64 on the mixed path
+    bool mixed_cheb = o.precision == IPM_PREC_MIXED && !(o.kernel_flags & 4);
+    bool mixed = o.precision == IPM_PREC_MIXED && !(o.kernel_flags & 8);
     int p1 = ph_begin(1);
-    if (mixed) cheb_apply<float, double>(r, dg.thy32, z, o.cheb_steps, cheb32);
+    if (mixed_cheb) cheb_apply<float, double>(r, dg.thy32, z, o.cheb_steps, cheb32);
     else cheb_apply<double, double>(r, dg.thy, z, o.cheb_steps, cheb64);
     ph_end(p1);
     int p2 = ph_begin(2);
@@ -599,7 +601,7 @@ struct ipm_solver {
   }
 
   void setup_precond(const ipm_options& o) {
-    if (o.precision == IPM_PREC_MIXED) mg_setup(mg32, dg.mh32);
+    if (o.precision == IPM_PREC_MIXED && !(o.kernel_flags & 8)) mg_setup(mg32, dg.mh32);
     else mg_setup(mg64, dg.mh);
   }
 
@@ -665,7 +667,8 @@ struct ipm_solver {
     long long key = ((long long)o.precision << 40) ^ ((long long)tri << 39) ^
                     ((long long)o.cheb_steps << 30) ^ ((long long)o.vcycles << 24) ^
                     ((long long)o.smooth_pre << 16) ^ ((long long)o.smooth_post << 8) ^
-                    ((long long)(fused ? 1 : 0) << 4) ^ (long long)(size_t)stream;
+                    ((long long)(fused ? 1 : 0) << 4) ^ ((long long)o.kernel_flags << 48) ^
+                    (long long)(size_t)stream;
     bool graphs = use_graphs && !prof_on && !phases_on;
     if (!graphs) {
       arnoldi_body(o, j, stride, len, tri);
