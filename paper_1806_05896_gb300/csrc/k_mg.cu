@@ -124,7 +124,48 @@ __global__ void k_mg_zero(GridDesc g, T* __restrict__ x) {
   x[c] = T(0);
 }
 
+// Outer step of the mixed-precision multigrid solve on the finest level:
+// x_new = x_prev + e (x_prev may be null = 0) in FP64, and, if r32 is given,
+// r32 = b - (L + diag(m)) x_new in FP64 rounded to FP32 (the next FP32 cycle's
+// right-hand side). The stencil reads x_prev + e at the neighbours directly.
+__global__ void k_mg_outer(GridDesc g, Stencil<double> st, OpL L, const double* __restrict__ xprev,
+                           const float* __restrict__ e, const double* __restrict__ b,
+                           const double* __restrict__ m, double* __restrict__ xnew,
+                           float* __restrict__ r32) {
+  int i, j, k;
+  long long c;
+  if (!interior_node(g, i, j, k, c)) return;
+  struct Sum {
+    const double* a;
+    const float* e;
+    IPM_D double operator()(long long q) const { return (a ? a[q] : 0.0) + (double)e[q]; }
+  } xn{xprev, e};
+  double x = xn(c);
+  xnew[c] = x;
+  if (r32) {
+    double ax;
+    if (L.coef == nullptr) {
+      ax = st.stiff_f(xn, c);
+    } else {
+      ax = 0.0;
+#pragma unroll
+      for (int o = 0; o < 9; ++o) {
+        long long off = (long long)(o / 3 - 1) * st.p + (o % 3 - 1);
+        ax += L.coef[o * g.field + c] * xn(c + off);
+      }
+    }
+    r32[c] = (float)(b[c] - (ax + m[c] * x));
+  }
+}
+
 }  // namespace
+
+void launch_mg_outer(const GridDesc& g, OpL L, const double* xprev, const float* e,
+                     const double* b, const double* m, double* xnew, float* r32, cudaStream_t s) {
+  count_launches(1);
+  k_mg_outer<<<interior_grid(g), interior_block(), 0, s>>>(g, make_stencil<double>(g), L, xprev, e,
+                                                           b, m, xnew, r32);
+}
 
 template <typename T>
 void launch_mg_smooth(const GridDesc& g, OpL L, const T* xin, T* xout, const T* b, const T* m,

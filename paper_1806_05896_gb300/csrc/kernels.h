@@ -107,6 +107,8 @@ template <typename T>
 void launch_mg_jinv(const GridDesc& g, OpL L, const T* m, double omega, T* jinv, cudaStream_t s);
 template <typename T>
 void launch_mg_zero(const GridDesc& g, T* x, cudaStream_t s);
+void launch_mg_outer(const GridDesc& g, OpL L, const double* xprev, const float* e,
+                     const double* b, const double* m, double* xnew, float* r32, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
 // k_mg_fused.cu (2D Poisson: tiled multi-sweep kernels and a one-CTA coarse cycle)

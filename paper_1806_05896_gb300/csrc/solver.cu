@@ -69,6 +69,7 @@ struct ipm_solver {
   float* cheb32[4] = {};
   MGHier<double> mg64;
   MGHier<float> mg32;
+  double *mgb64 = nullptr, *mgx64[2] = {};  // FP64 right-hand side and iterates of the mixed solve
   double *part = nullptr, *dout = nullptr, *sc = nullptr, *kdev = nullptr;
   long long part_rows = 0;
   double* hbuf = nullptr;  // pinned
@@ -305,6 +306,9 @@ struct ipm_solver {
     for (int i = 0; i < 4; ++i) cheb32[i] = alloc<float>(f);
     build_mg(mg64);
     build_mg(mg32);
+    mgb64 = alloc<double>(f);
+    mgx64[0] = alloc<double>(f);
+    mgx64[1] = alloc<double>(f);
     part_rows = std::max<long long>(interior_blocks(g), 8 * kRedBlocks);
     part = alloc<double>(part_rows * 8);
     dout = alloc<double>(64);
@@ -481,6 +485,34 @@ struct ipm_solver {
     }
   }
 
+  // Mixed-precision multigrid solve of (L + M_hat) x = b64 (FP64 right-hand side):
+  // the cycle iterate and its residual stay in FP64 on the finest level, every V-cycle
+  // runs in FP32 on the correction equation from zero: x_{k+1} = x_k + V(b - A x_k),
+  // the same operator as `vcycles` cycles from zero. In FP32 alone the finest-level
+  // residual of a smooth iterate loses its digits to cancellation in the stiffness
+  // stencil (8 x_c - neighbours ~ h^2 x''), which slows the outer Krylov method.
+  void mg_solve_mixed(const double* b64, double* out, int tr, const ipm_options& o) {
+    MGLevel<float>& L0 = mg32.lv[0];
+    const int cycles = std::max(1, o.vcycles);
+    launch_convert<double, float>(g, b64, L0.b, stream);
+    const double* xprev = nullptr;
+    int xb = 0;
+    for (int c = 0; c < cycles; ++c) {
+      float* e;
+      if (fused_mg()) {
+        vcycle_fused(mg32, true, o);
+      } else {
+        vcycle(mg32, 0, true, tr, o);
+      }
+      e = L0.x[mg32.cur[0]];
+      const bool last = c == cycles - 1;
+      double* xnew = last ? out : mgx64[xb];
+      launch_mg_outer(g, opL(), xprev, e, b64, dg.mh, xnew, last ? nullptr : L0.b, stream);
+      xprev = xnew;
+      xb ^= 1;
+    }
+  }
+
   // x = (vcycles V-cycles from zero) applied to lv[0].b; returns the level-0 iterate
   template <typename T>
   T* mg_solve(MGHier<T>& mg, int tr, const ipm_options& o) {
@@ -568,22 +600,22 @@ struct ipm_solver {
     int p2 = ph_begin(2);
     launch_zblock(g, alpha * mass_diag(g), r + f, r + 2 * f, dg.thw, dg.thv, z + f, z + 2 * f,
                   stream);
-    if (mixed) launch_coupling<float>(g, opL(), z, z + f, z + 2 * f, r + 3 * f, tri, mg32.lv[0].b, stream);
+    if (mixed) launch_coupling<double>(g, opL(), z, z + f, z + 2 * f, r + 3 * f, tri, mgb64, stream);
     else launch_coupling<double>(g, opL(), z, z + f, z + 2 * f, r + 3 * f, tri, mg64.lv[0].b, stream);
     ph_end(p2);
     if (mixed) {
+      // S_hat^{-1} t = (L + M_hat)^{-T} (M + Theta_y) (L + M_hat)^{-1} t, FP32 cycles with
+      // FP64 outer residuals; s1 is kept in FP64 for the (M + Theta_y) product
+      double* s1 = mg64.lv[0].r;  // an FP64 field of the finest level, free during this solve
       int p3 = ph_begin(3);
-      float* s1 = mg_solve(mg32, 0, o);
+      mg_solve_mixed(mgb64, s1, 0, o);
       ph_end(p3);
       int p4 = ph_begin(4);
-      launch_mass_theta<float>(g, s1, dg.thy32, mg32.lv[0].b, stream);
+      launch_mass_theta<double>(g, s1, dg.thy, mgb64, stream);
       ph_end(p4);
       int p5 = ph_begin(3);
-      float* xp = mg_solve(mg32, 1, o);
+      mg_solve_mixed(mgb64, z + 3 * f, 1, o);
       ph_end(p5);
-      int p6 = ph_begin(4);
-      launch_convert<float, double>(g, xp, z + 3 * f, stream);
-      ph_end(p6);
     } else {
       int p3 = ph_begin(3);
       double* s1 = mg_solve(mg64, 0, o);
