@@ -270,7 +270,7 @@ def run_ours(args, rank, world):
         avg_s = prof[0] / prof[1] / 1000.0
         achieved = prof[2] / avg_s / 1e9
         roof = {"bound": "hbm",
-                "kernel": "k_mg2_pre_restrict<float> (finest level: 5 Jacobi sweeps + residual + restriction)",
+                "kernel": "k_mg2_pre_restrict<float,64,32> (finest level: 5 Jacobi sweeps + residual + restriction)",
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": None, "peak_kind": peak_kind, "sampled_launches": prof[1],
                 "avg_launch_us": avg_s * 1e6, "algorithmic_bytes_per_launch": prof[2]}

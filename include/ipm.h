@@ -161,8 +161,10 @@ long long ipm_launch_count(void);
  * enable = 1 starts recording a CUDA event pair around every `every`-th launch on
  * the solver's stream (and clears earlier samples); enable = 0 stops.
  * ipm_profile_read returns the summed event time of the sampled launches, their
- * number, and the algorithmic bytes one launch moves (read x, b, m, jinv and write x
- * once per unknown, in the precision of the mixed path: 4-byte values). */
+ * number, and the average algorithmic bytes one sampled launch moves per the values it
+ * reads and writes once per unknown (fused 2D kernel: x (unless it starts from zero), b, m
+ * read, x and a quarter-size coarse right-hand side written; per-sweep kernel: x, b, m,
+ * jinv read, x written), in the precision of the last solve. */
 int ipm_profile_smoother(ipm_solver* s, int enable, int every);
 int ipm_profile_read(ipm_solver* s, double* total_ms, long long* launches, double* bytes_per_launch);
 /* Per-stage CUDA-event timing of the Krylov iteration (disables graph replay while on).

@@ -86,6 +86,7 @@ struct ipm_solver {
   int prof_used = 0;
   double prof_ms = 0.0;
   long long prof_count = 0;
+  long long prof_zero = 0;  // sampled launches that started from a zero iterate
   double ph_ms[16] = {};
   long long ph_count[16] = {};
 
@@ -132,9 +133,10 @@ struct ipm_solver {
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, prof_ev[i], prof_ev[i + 1]));
       int tag = prof_tag[i / 2];
-      if (tag == 0) {
+      if (tag == 0 || tag == 13) {
         prof_ms += ms;
         ++prof_count;
+        if (tag == 13) ++prof_zero;
       } else {
         ph_ms[tag] += ms;
         ++ph_count[tag];
@@ -172,8 +174,8 @@ struct ipm_solver {
     CK(cudaEventRecord(prof_ev[slot + 1], stream));
     --prof_open;
   }
-  // sampled smoother timing (tag 0)
-  int prof_begin() {
+  // sampled smoother timing (tag 0; tag 13 for launches that start from a zero iterate)
+  int prof_begin(int tag = 0) {
     if (!prof_on || phases_on || (prof_seen++ % prof_every) != 0) return -1;
     ensure_events();
     if (prof_used + 2 > (int)prof_ev.size() && prof_open == 0) prof_flush();
@@ -181,7 +183,7 @@ struct ipm_solver {
     int slot = prof_used;
     prof_used += 2;
     ++prof_open;
-    prof_tag[slot / 2] = 0;
+    prof_tag[slot / 2] = tag;
     CK(cudaEventRecord(prof_ev[slot], stream));
     return slot;
   }
@@ -452,7 +454,7 @@ struct ipm_solver {
     for (int l = 0; l < lc; ++l) {
       MGLevel<T>& L = mg.lv[l];
       int& cur = mg.cur[l];
-      int pr = (l == 0 && !zero_x) ? prof_begin() : -1;
+      int pr = l == 0 ? prof_begin(zero_x ? 13 : 0) : -1;
       int ph = ph_begin(l == 0 ? 9 : 11);
       launch_mg2_pre_restrict<T>(L.g, mg.lv[l + 1].g, L.x[cur], L.x[1 - cur], L.b, L.m,
                                  mg.lv[l + 1].b, omega(), o.smooth_pre, (l > 0 || zero_x) ? 1 : 0,
@@ -1166,6 +1168,7 @@ int ipm_profile_smoother(ipm_solver* s, int enable, int every) {
     s->prof_seen = 0;
     s->prof_ms = 0.0;
     s->prof_count = 0;
+    s->prof_zero = 0;
     return IPM_OK;
   });
 }
@@ -1197,10 +1200,12 @@ int ipm_profile_read(ipm_solver* s, double* total_ms, long long* launches, doubl
     if (launches) *launches = s->prof_count;
     // algorithmic bytes of one sampled finest-level launch, per unknown: fused 2D kernel
     // (nu sweeps + residual + restriction) reads x, b, m and writes x and a quarter-size
-    // coarse right-hand side (4.25 values); a single sweep reads x, b, m, jinv and writes x (5)
+    // coarse right-hand side (4.25 values; 3.25 when it starts from zero and reads no x);
+    // a single sweep reads x, b, m, jinv and writes x (5)
     long long m = s->g.n - 2;
     long long unknowns = s->g.dim == 3 ? m * m * m : m * m;
-    double vals = s->fused_mg() ? 4.25 : 5.0;
+    double zfrac = s->prof_count ? (double)s->prof_zero / (double)s->prof_count : 0.0;
+    double vals = s->fused_mg() ? 4.25 - zfrac : 5.0;
     double word = s->last_precision == IPM_PREC_MIXED ? 4.0 : 8.0;
     if (bytes_per_launch) *bytes_per_launch = vals * (double)unknowns * word;
     return IPM_OK;
