@@ -131,7 +131,7 @@ __global__ void k_mg_zero(GridDesc g, T* __restrict__ x) {
 __global__ void k_mg_outer(GridDesc g, Stencil<double> st, OpL L, const double* __restrict__ xprev,
                            const float* __restrict__ e, const double* __restrict__ b,
                            const double* __restrict__ m, double* __restrict__ xnew,
-                           float* __restrict__ r32) {
+                           float* __restrict__ r32, int transpose) {
   int i, j, k;
   long long c;
   if (!interior_node(g, i, j, k, c)) return;
@@ -151,7 +151,8 @@ __global__ void k_mg_outer(GridDesc g, Stencil<double> st, OpL L, const double* 
 #pragma unroll
       for (int o = 0; o < 9; ++o) {
         long long off = (long long)(o / 3 - 1) * st.p + (o % 3 - 1);
-        ax += L.coef[o * g.field + c] * xn(c + off);
+        long long idx = transpose ? (long long)(8 - o) * g.field + c + off : (long long)o * g.field + c;
+        ax += L.coef[idx] * xn(c + off);
       }
     }
     r32[c] = (float)(b[c] - (ax + m[c] * x));
@@ -161,10 +162,11 @@ __global__ void k_mg_outer(GridDesc g, Stencil<double> st, OpL L, const double* 
 }  // namespace
 
 void launch_mg_outer(const GridDesc& g, OpL L, const double* xprev, const float* e,
-                     const double* b, const double* m, double* xnew, float* r32, cudaStream_t s) {
+                     const double* b, const double* m, double* xnew, float* r32, int transpose,
+                     cudaStream_t s) {
   count_launches(1);
   k_mg_outer<<<interior_grid(g), interior_block(), 0, s>>>(g, make_stencil<double>(g), L, xprev, e,
-                                                           b, m, xnew, r32);
+                                                           b, m, xnew, r32, transpose);
 }
 
 template <typename T>

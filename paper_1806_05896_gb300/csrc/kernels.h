@@ -108,7 +108,8 @@ void launch_mg_jinv(const GridDesc& g, OpL L, const T* m, double omega, T* jinv,
 template <typename T>
 void launch_mg_zero(const GridDesc& g, T* x, cudaStream_t s);
 void launch_mg_outer(const GridDesc& g, OpL L, const double* xprev, const float* e,
-                     const double* b, const double* m, double* xnew, float* r32, cudaStream_t s);
+                     const double* b, const double* m, double* xnew, float* r32, int transpose,
+                     cudaStream_t s);
 
 // ----------------------------------------------------------------------------
 // k_mg_fused.cu (2D Poisson: tiled multi-sweep kernels and a one-CTA coarse cycle)
@@ -148,6 +149,14 @@ template <typename T, typename Ti, typename To>
 void launch_cheb2_block(const GridDesc& g, const ChebSteps& cs, const Ti* b, const T* thy,
                         const T* xc_in, const T* xp_in, T* xc_out, T* xp_out, To* final_out,
                         int first, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// k_cd.cu (convection-diffusion + SUPG stencil, Galerkin coarse operators)
+// ----------------------------------------------------------------------------
+void launch_cd_coef(const GridDesc& g, double eps, double* coef, cudaStream_t s);
+void launch_galerkin(const GridDesc& gf, const GridDesc& gc, const double* cf, double* cc,
+                     cudaStream_t s);
+void launch_to_float(long long n, const double* x, float* y, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
 // k_vec.cu (Krylov vector kernels over whole field blocks, deterministic)

@@ -70,6 +70,8 @@ struct ipm_solver {
   MGHier<double> mg64;
   MGHier<float> mg32;
   double *mgb64 = nullptr, *mgx64[2] = {};  // FP64 right-hand side and iterates of the mixed solve
+  // stored operator per multigrid level (convection-diffusion); empty for Poisson
+  std::vector<OpL> lvop;
   double *part = nullptr, *dout = nullptr, *sc = nullptr, *kdev = nullptr;
   long long part_rows = 0;
   double* hbuf = nullptr;  // pinned
@@ -209,7 +211,8 @@ struct ipm_solver {
     own = nullptr;
   }
 
-  OpL opL() const { return OpL{nullptr, nullptr}; }
+  OpL opL() const { return lvop.empty() ? OpL{nullptr, nullptr} : lvop[0]; }
+  OpL opl(int l) const { return lvop.empty() ? OpL{nullptr, nullptr} : lvop[l]; }
   IpmProblem problem() const {
     IpmProblem pb;
     pb.alpha = alpha;
@@ -268,7 +271,10 @@ struct ipm_solver {
     if (!(a > 0.0) || !(b >= 0.0) || !std::isfinite(a) || !std::isfinite(b))
       throw IpmError{IPM_EINVAL, "need alpha > 0 and beta >= 0"};
     pde = p ? *p : ipm_pde{IPM_POISSON, 1.0, 0};
-    if (pde.kind != IPM_POISSON) throw IpmError{IPM_EINVAL, "only the Poisson state equation is built"};
+    if (pde.kind != IPM_POISSON && pde.kind != IPM_CONVDIFF_SUPG)
+      throw IpmError{IPM_EINVAL, "unknown state equation"};
+    if (pde.kind == IPM_CONVDIFF_SUPG && (dim != 2 || !(pde.eps > 0.0) || pde.wind != 0))
+      throw IpmError{IPM_EINVAL, "convection-diffusion needs dim 2, eps > 0 and wind 0"};
     g = make_grid(dim, n);
     alpha = a;
     beta = b;
@@ -308,6 +314,7 @@ struct ipm_solver {
     for (int i = 0; i < 4; ++i) cheb32[i] = alloc<float>(f);
     build_mg(mg64);
     build_mg(mg32);
+    if (pde.kind == IPM_CONVDIFF_SUPG) build_cd_operators();
     mgb64 = alloc<double>(f);
     mgx64[0] = alloc<double>(f);
     mgx64[1] = alloc<double>(f);
@@ -318,6 +325,21 @@ struct ipm_solver {
     kdev = alloc<double>(4 * (kMaxRestart + 2));
     dense = alloc<double>(nn());
     set_bounds(bd);
+  }
+
+  // convection-diffusion: SUPG stencil on the finest grid, Galerkin P^T L P below
+  void build_cd_operators() {
+    lvop.resize(mg64.nlev);
+    for (int l = 0; l < mg64.nlev; ++l) {
+      const GridDesc& gl = mg64.lv[l].g;
+      double* c64 = alloc<double>(9 * gl.field);
+      float* c32 = alloc<float>(9 * gl.field);
+      if (l == 0) launch_cd_coef(gl, pde.eps, c64, stream);
+      else launch_galerkin(mg64.lv[l - 1].g, gl, lvop[l - 1].coef, c64, stream);
+      launch_to_float(9 * gl.field, c64, c32, stream);
+      lvop[l] = OpL{c64, c32};
+    }
+    sync();
   }
 
   // bounds -> fields ya, yb, zbw = max(u_b, 0) = u_b, zbv = -min(u_a, 0) = -u_a
@@ -401,7 +423,7 @@ struct ipm_solver {
     for (int l = 1; l < mg.nlev; ++l)
       launch_mg_restrict<T>(mg.lv[l - 1].g, mg.lv[l].g, mg.lv[l - 1].m, mg.lv[l].m, stream);
     for (int l = 0; l < mg.nlev; ++l)
-      launch_mg_jinv<T>(mg.lv[l].g, opL(), mg.lv[l].m, omega(), mg.lv[l].jinv, stream);
+      launch_mg_jinv<T>(mg.lv[l].g, opl(l), mg.lv[l].m, omega(), mg.lv[l].jinv, stream);
   }
 
   template <typename T>
@@ -409,26 +431,26 @@ struct ipm_solver {
     MGLevel<T>& L = mg.lv[l];
     int& cur = mg.cur[l];
     if (l == mg.nlev - 1) {
-      launch_mg_coarsest<T>(L.g, opL(), L.b, L.m, L.x[cur], stream);
+      launch_mg_coarsest<T>(L.g, opl(l), L.b, L.m, L.x[cur], stream);
       return;
     }
     bool z = zero_x;
     for (int i = 0; i < o.smooth_pre; ++i) {
       int pr = (l == 0 && !z) ? prof_begin() : -1;
-      launch_mg_smooth<T>(L.g, opL(), L.x[cur], L.x[1 - cur], L.b, L.m, L.jinv, z, tr, stream);
+      launch_mg_smooth<T>(L.g, opl(l), L.x[cur], L.x[1 - cur], L.b, L.m, L.jinv, z, tr, stream);
       prof_end(pr);
       cur = 1 - cur;
       z = false;
     }
     if (z) launch_mg_zero<T>(L.g, L.x[cur], stream);
-    launch_mg_residual<T>(L.g, opL(), L.x[cur], L.b, L.m, L.r, tr, stream);
+    launch_mg_residual<T>(L.g, opl(l), L.x[cur], L.b, L.m, L.r, tr, stream);
     MGLevel<T>& C = mg.lv[l + 1];
     launch_mg_restrict<T>(L.g, C.g, L.r, C.b, stream);
     vcycle(mg, l + 1, true, tr, o);
     launch_mg_prolong_add<T>(L.g, C.g, C.x[mg.cur[l + 1]], L.x[cur], stream);
     for (int i = 0; i < o.smooth_post; ++i) {
       int pr = l == 0 ? prof_begin() : -1;
-      launch_mg_smooth<T>(L.g, opL(), L.x[cur], L.x[1 - cur], L.b, L.m, L.jinv, 0, tr, stream);
+      launch_mg_smooth<T>(L.g, opl(l), L.x[cur], L.x[1 - cur], L.b, L.m, L.jinv, 0, tr, stream);
       prof_end(pr);
       cur = 1 - cur;
     }
@@ -444,7 +466,7 @@ struct ipm_solver {
       if (mg.lv[l].g.n <= limit) return l;
     return mg.nlev - 1;
   }
-  bool fused_mg() const { return g.dim == 2 && fused && nu_fits; }
+  bool fused_mg() const { return g.dim == 2 && fused && nu_fits && lvop.empty(); }
   bool nu_fits = true;  // fused tiles hold up to 8 sweeps of halo
 
   // one V-cycle with the fused kernels (same operator, smoother and transfers)
@@ -509,7 +531,7 @@ struct ipm_solver {
       e = L0.x[mg32.cur[0]];
       const bool last = c == cycles - 1;
       double* xnew = last ? out : mgx64[xb];
-      launch_mg_outer(g, opL(), xprev, e, b64, dg.mh, xnew, last ? nullptr : L0.b, stream);
+      launch_mg_outer(g, opL(), xprev, e, b64, dg.mh, xnew, last ? nullptr : L0.b, tr, stream);
       xprev = xnew;
       xb ^= 1;
     }

@@ -22,7 +22,8 @@ pytestmark = pytest.mark.gpu
 def _run_pair(wl, k, common=False, **opts):
     qp = Q.from_workload(wl)
     ref = oipm.solve(qp, sigma=wl.sigma, n_iter=k, common_step=common)
-    s = ipm.Solver(wl.dim, wl.n, wl.alpha, wl.beta, wl.ua, wl.ub, wl.ya, wl.yb)
+    s = ipm.Solver(wl.dim, wl.n, wl.alpha, wl.beta, wl.ua, wl.ub, wl.ya, wl.yb, kind=wl.kind,
+                   eps=wl.eps)
     s.set_data(wl.yd)
     rep = s.solve(stop=ipm.STOP_FIXED, fixed_iters=k, sigma=wl.sigma, common_step=int(common),
                   **opts)
@@ -122,6 +123,21 @@ def test_poisson_3d(n):
     got, want, rep, _, _ = _run_pair(wl, k)
     for f in ("y", "u", "p"):
         assert rel(got[f], want[f]) < 1e-8, (f, rel(got[f], want[f]))
+
+
+@pytest.mark.parametrize("n,krylov,prec,tol", [(33, ipm.KRYLOV_GMRES_PT, ipm.PREC_FP64, 1e-8),
+                                                (65, ipm.KRYLOV_GMRES_PT, ipm.PREC_FP64, 1e-8),
+                                                (33, ipm.KRYLOV_MINRES_PD, ipm.PREC_FP64, 1e-8),
+                                                (65, ipm.KRYLOV_GMRES_PT, ipm.PREC_MIXED, 1e-6)])
+def test_convection_diffusion_supg(n, krylov, prec, tol):
+    """Section 5.2 problem (eps = 1/50, recirculating wind, SUPG, u in [-2, 1.5],
+    sigma = 0.25) at small grids against the oracle's assembled SUPG matrices."""
+    wl = W.workload_c4(n=n)
+    k = _iters_to(wl, 1e-10 if prec == ipm.PREC_FP64 else 1e-6, True)
+    got, want, rep, _, _ = _run_pair(wl, k, True, krylov=krylov, precision=prec, krylov_tol=1e-12)
+    for f in ("y", "u", "p"):
+        assert rel(got[f], want[f]) < tol, (f, rel(got[f], want[f]))
+    assert rep["krylov_relres_max"] < 2e-12
 
 
 def test_single_unknown_and_tiny_grids():

@@ -20,28 +20,33 @@ pytestmark = pytest.mark.gpu
 CASES = [(2, 3), (2, 5), (2, 33), (2, 65), (2, 129), (3, 3), (3, 5), (3, 17), (3, 33)]
 
 
-def _qp(dim, n, alpha=1e-2, beta=1e-3, ua=-2.0, ub=1.5, **kw):
-    return Q.build(dim, n, alpha, beta, ua, ub, **kw)
+EPS_CD = 1.0 / 50.0
 
 
-def _solver(qp, ua=-2.0, ub=1.5, **kw):
-    return ipm.Solver(qp.dim, qp.n, qp.alpha, qp.beta, ua, ub, **kw)
+def _qp(dim, n, alpha=1e-2, beta=1e-3, ua=-2.0, ub=1.5, kind="poisson", **kw):
+    return Q.build(dim, n, alpha, beta, ua, ub, kind=kind, eps=EPS_CD, **kw)
+
+
+def _solver(qp, ua=-2.0, ub=1.5, kind="poisson", **kw):
+    return ipm.Solver(qp.dim, qp.n, qp.alpha, qp.beta, ua, ub, kind=kind, eps=EPS_CD, **kw)
 
 
 def _thetas(nI, rng, spread=4.0):
     return [10.0 ** rng.uniform(-spread, spread, nI) for _ in range(3)]
 
 
-@pytest.mark.parametrize("dim,n", CASES)
-def test_newton_apply_matches_oracle(dim, n):
+@pytest.mark.parametrize("dim,n,kind", [c + ("poisson",) for c in CASES] +
+                         [(2, 5, "cd"), (2, 33, "cd"), (2, 65, "cd"), (2, 257, "cd")])
+def test_newton_apply_matches_oracle(dim, n, kind):
+    """Saddle operator of (NewtonSystem), with L and L^T for the convection-diffusion case."""
     torch = torch_cuda()
-    qp = _qp(dim, n)
+    qp = _qp(dim, n, kind=kind)
     rng = np.random.default_rng(n + dim)
     th = _thetas(qp.nI, rng)
     x = rng.standard_normal(4 * qp.nI)
     A = oipm.newton_matrix(qp, *th)
     ref = A @ x
-    s = _solver(qp)
+    s = _solver(qp, kind=kind)
     out = torch.empty(4 * n ** dim, dtype=torch.float64, device="cuda")
     s.newton_apply(*[dev(embed(qp, t)) for t in th], dev(embed4(qp, x)), out)
     got = interior4(qp, host(out))
@@ -70,6 +75,28 @@ def test_chebyshev_matches_oracle(dim, n):
     s.chebyshev(20, dev(embed(qp, thy)), dev(embed(qp, b)), x)
     got = host(x)[qp.idx]
     assert rel(got, ref) < 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("dim,n", [(2, 33), (2, 129)])
+def test_vcycle_convdiff_contracts_and_transposes(dim, n):
+    """Multigrid on L + diag(m) with the SUPG operator and Galerkin coarse operators: three
+    cycles reduce the error, and the cycle on L^T + diag(m) is the adjoint of the cycle on
+    L + diag(m) (Jacobi smoothing with equal pre/post counts)."""
+    torch = torch_cuda()
+    qp = _qp(dim, n, kind="cd")
+    rng = np.random.default_rng(5)
+    m = qp.dM * 10.0 ** rng.uniform(-6, 3, qp.nI)
+    A = (qp.L + sp.diags(m)).tocsc()
+    b = rng.standard_normal(qp.nI)
+    u = rng.standard_normal(qp.nI)
+    xs = spla.spsolve(A, b)
+    s = _solver(qp, kind="cd")
+    out = torch.empty(n ** dim, dtype=torch.float64, device="cuda")
+    vb = host(s.vcycle(False, dev(embed(qp, m)), dev(embed(qp, b)), out))[qp.idx]
+    assert np.linalg.norm(vb - xs) < 0.1 * np.linalg.norm(xs)
+    vtu = host(s.vcycle(True, dev(embed(qp, m)), dev(embed(qp, u)), out))[qp.idx]
+    assert abs(u @ vb - vtu @ b) < 1e-11 * np.linalg.norm(u) * np.linalg.norm(vb)
     s.close()
 
 
