@@ -327,15 +327,16 @@ struct ipm_solver {
     set_bounds(bd);
   }
 
-  // convection-diffusion: SUPG stencil on the finest grid, Galerkin P^T L P below
+  // convection-diffusion: the SUPG operator rediscretised on every multigrid level, each
+  // with its own element Peclet numbers. (Galerkin P^T L P operators keep the fine grid's
+  // SUPG parameter and are under-stabilised on coarse grids, where damped Jacobi diverges.)
   void build_cd_operators() {
     lvop.resize(mg64.nlev);
     for (int l = 0; l < mg64.nlev; ++l) {
       const GridDesc& gl = mg64.lv[l].g;
       double* c64 = alloc<double>(9 * gl.field);
       float* c32 = alloc<float>(9 * gl.field);
-      if (l == 0) launch_cd_coef(gl, pde.eps, c64, stream);
-      else launch_galerkin(mg64.lv[l - 1].g, gl, lvop[l - 1].coef, c64, stream);
+      launch_cd_coef(gl, pde.eps, c64, stream);
       launch_to_float(9 * gl.field, c64, c32, stream);
       lvop[l] = OpL{c64, c32};
     }

@@ -78,15 +78,16 @@ def test_chebyshev_matches_oracle(dim, n):
     s.close()
 
 
-@pytest.mark.parametrize("dim,n", [(2, 33), (2, 129)])
-def test_vcycle_convdiff_contracts_and_transposes(dim, n):
+@pytest.mark.parametrize("dim,n,mlog", [(2, 33, (-6, 3)), (2, 129, (-6, 3)), (2, 33, (-3, -3)),
+                                        (2, 257, (-3, -3))])
+def test_vcycle_convdiff_contracts_and_transposes(dim, n, mlog):
     """Multigrid on L + diag(m) with the SUPG operator and Galerkin coarse operators: three
     cycles reduce the error, and the cycle on L^T + diag(m) is the adjoint of the cycle on
     L + diag(m) (Jacobi smoothing with equal pre/post counts)."""
     torch = torch_cuda()
     qp = _qp(dim, n, kind="cd")
     rng = np.random.default_rng(5)
-    m = qp.dM * 10.0 ** rng.uniform(-6, 3, qp.nI)
+    m = qp.dM * 10.0 ** rng.uniform(mlog[0], mlog[1], qp.nI)
     A = (qp.L + sp.diags(m)).tocsc()
     b = rng.standard_normal(qp.nI)
     u = rng.standard_normal(qp.nI)
