@@ -301,6 +301,9 @@ def run_ours(args, rank, world):
         "roofline": roof,
         "clocks": clocks,
     }
+    if rank == 0 and not args.no_extra:
+        line["other_configs"] = other_configs(ipm, W, np, stream)
+        line["serving"] = serving(ipm, W, np, args.serve_requests)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline("ours")
     if rank == 0:
@@ -309,6 +312,80 @@ def run_ours(args, rank, world):
         s.close()
     if dist:
         dist.destroy_process_group()
+
+
+def _timed_solve(ipm, s, o, reps=2):
+    import torch
+    s.solve(o)  # warm-up (graph capture)
+    ms = []
+    rep = None
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        rep = s.solve(o)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return min(ms), rep
+
+
+def other_configs(ipm, W, np, stream):
+    """One timed solve each of the 513^2 convection-diffusion and 129^3 Poisson configurations."""
+    out = {}
+    for name, wl, kw in (("cd2d_513_supg", W.workload_c4(n=513), dict(precision=ipm.PREC_MIXED)),
+                         ("poisson3d_129", W.workload_c3(n=129), dict(precision=ipm.PREC_MIXED))):
+        s = ipm.Solver(wl.dim, wl.n, wl.alpha, wl.beta, wl.ua, wl.ub, wl.ya, wl.yb, kind=wl.kind,
+                       eps=wl.eps)
+        s.set_data(wl.yd)
+        o = ipm.default_options(stop=ipm.STOP_KKT, kkt_tol=1e-6, common_step=1, sigma=wl.sigma,
+                                max_ipm=60, **kw)
+        ms, rep = _timed_solve(ipm, s, o)
+        out[name] = {"ms_per_solve": ms, "solves_per_s": 1000.0 / ms, "ipm_iters": rep["ipm_iters"],
+                     "krylov_iters_per_ipm": rep["krylov_iters_total"] / max(rep["ipm_iters"], 1),
+                     "kkt_rel": rep["kkt_rel"], "precision": "mixed", "krylov": "FGMRES + P_T"}
+        s.close()
+    return out
+
+
+def serving(ipm, W, np, num):
+    """Seeded request stream (2D 65..513, 3D 33..65, 70/30 Poisson/CD) through the native
+    server: a closed-loop burst (saturation throughput) and an open loop at 0.8x that rate."""
+    reqs = W.serving_stream(num, seed=0)
+    opts = dict(precision=ipm.PREC_MIXED, stop=ipm.STOP_KKT, kkt_tol=1e-6, common_step=1,
+                max_ipm=60, restart=30)
+    sv = ipm.Server(workers=4, budget_bytes=96 << 30)
+
+    def submit(r):
+        return sv.submit(r["dim"], r["n"], r["alpha"], r["beta"], r["ua"], r["ub"], r["yd"],
+                         kind=r["kind"], eps=r["eps"], sigma=r["sigma"], **opts)
+    seen = {}
+    for r in reqs:  # warm: one request per distinct grid and state equation
+        seen.setdefault((r["dim"], r["n"], r["kind"]), r)
+    for t in [submit(r) for r in seen.values()]:
+        sv.wait(t)
+    t0 = time.perf_counter()
+    tickets = [submit(r) for r in reqs]
+    lat = [sv.wait(t)[2] for t in tickets]
+    burst_s = time.perf_counter() - t0
+    sat = num / burst_s
+    gap = 1.0 / (0.8 * sat)
+    t0 = time.perf_counter()
+    tickets = []
+    for r in reqs:
+        time.sleep(r["gap"] * gap)
+        tickets.append(submit(r))
+    lat2 = [sv.wait(t)[2] for t in tickets]
+    open_s = time.perf_counter() - t0
+    sv.close()
+    pct = lambda xs, q: float(np.percentile(np.asarray(xs), q)) * 1000.0
+    return {"requests": num, "workers": 4,
+            "saturation": {"solves_per_s": sat, "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99)},
+            "open_loop_0.8x": {"offered_per_s": 0.8 * sat, "solves_per_s": num / open_s,
+                               "p50_ms": pct(lat2, 50), "p99_ms": pct(lat2, 99)},
+            "mix": "2D {65,129,257,513}^2, 3D {33,65}^3, Poisson/CD 70/30 (CD 2D only), "
+                   "log-uniform alpha, beta, Gaussian-sum y_d, mixed precision, kkt_rel 1e-6"}
 
 
 def main():
@@ -320,6 +397,8 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--legs", default="all", choices=["all", "mixed"])
+    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=48)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

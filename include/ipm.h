@@ -124,6 +124,15 @@ void ipm_default_options(ipm_options* opt);
 int ipm_create(const ipm_grid* grid, const ipm_pde* pde, double alpha, double beta,
                const ipm_bounds* bounds, ipm_solver** out);
 
+/* Reuse a solver for a new problem on the same grid and state equation: new alpha, beta
+ * and bounds (validated as in ipm_create); ipm_set_data must follow before ipm_solve.
+ * Keeps all device memory. */
+int ipm_reset(ipm_solver* s, double alpha, double beta, const ipm_bounds* bounds);
+
+/* Device memory owned by the solver, in bytes (grows when a solve needs a larger
+ * Krylov basis). */
+size_t ipm_device_bytes(const ipm_solver* s);
+
 /* Use an existing CUDA stream (cudaStream_t passed as void*; NULL = the
  * solver's own stream). All device work of later calls is ordered on it. */
 int ipm_set_stream(ipm_solver* s, void* cuda_stream);
@@ -178,6 +187,36 @@ int ipm_profile_read(ipm_solver* s, double* total_ms, long long* launches, doubl
 int ipm_profile_phases(ipm_solver* s, int enable, double* ms, long long* counts, int nphases);
 const char* ipm_strerror(int code);
 const char* ipm_last_error(const ipm_solver* s);
+
+/* ---------------------------------------------------------------------------
+ * Serving: independent solves of many requests on one GPU. Worker threads each own a
+ * CUDA stream, so requests overlap on the device; a request is admitted when its solver
+ * fits the device-memory budget (solvers are pooled per grid and state equation, reset
+ * per request, and idle ones are evicted when another grid needs room). Results do not
+ * depend on what else runs: every kernel's reductions have a fixed order.
+ * --------------------------------------------------------------------------- */
+typedef struct ipm_server ipm_server;
+typedef struct {
+  ipm_grid grid;
+  ipm_pde pde;
+  double alpha, beta;
+  ipm_bounds bounds; /* scalar bounds only (nodal arrays are rejected) */
+  const double* yd;  /* host, n^d doubles, copied at submission */
+  ipm_options opt;
+} ipm_request;
+
+/* Start `workers` worker threads on the current device with a device-memory budget. */
+int ipm_server_create(int workers, size_t hbm_budget_bytes, ipm_server** out);
+/* Queue a request (returns at once). IPM_ENOMEM if it can never fit the budget. */
+int ipm_server_submit(ipm_server* sv, const ipm_request* rq, long long* ticket);
+/* Block until the request is done; copy its report and control (len = n^d doubles, may be
+ * NULL), its latency from submission to completion and its time in the queue (seconds).
+ * Returns the solve's status. A ticket can be waited for once. */
+int ipm_server_wait(ipm_server* sv, long long ticket, ipm_report* rep, double* u, size_t len,
+                    double* latency_s, double* queue_s);
+int ipm_server_stats(ipm_server* sv, size_t* bytes_in_use, int* solvers, long long* completed);
+/* Stop the workers (after the running solves) and free every pooled solver. */
+void ipm_server_destroy(ipm_server* sv);
 
 /* ---------------------------------------------------------------------------
  * Component entry points: one stage of the hot path on device buffers, for

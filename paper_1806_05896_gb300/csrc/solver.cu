@@ -343,6 +343,19 @@ struct ipm_solver {
     sync();
   }
 
+  // reuse the solver (same grid and state equation) for a new problem
+  void reset(double a, double b, const ipm_bounds* bd) {
+    if (!bd) throw IpmError{IPM_EINVAL, "null bounds"};
+    if (!(a > 0.0) || !(b >= 0.0) || !std::isfinite(a) || !std::isfinite(b))
+      throw IpmError{IPM_EINVAL, "need alpha > 0 and beta >= 0"};
+    set_bounds(bd);
+    alpha = a;
+    beta = b;
+    drop_graphs();  // captured kernels carry alpha-dependent arguments
+    has_data = false;
+    solved = false;
+  }
+
   // bounds -> fields ya, yb, zbw = max(u_b, 0) = u_b, zbv = -min(u_a, 0) = -u_a
   void set_bounds(const ipm_bounds* bd) {
     long long m = nn();
@@ -1104,6 +1117,16 @@ int ipm_create(const ipm_grid* grid, const ipm_pde* pde, double alpha, double be
   *out = s;
   return IPM_OK;
 }
+
+int ipm_reset(ipm_solver* s, double alpha, double beta, const ipm_bounds* bounds) {
+  if (!s) return IPM_EINVAL;
+  return guarded(s, [&] {
+    s->reset(alpha, beta, bounds);
+    return IPM_OK;
+  });
+}
+
+size_t ipm_device_bytes(const ipm_solver* s) { return s ? s->bytes : 0; }
 
 int ipm_set_stream(ipm_solver* s, void* stream) {
   if (!s) return IPM_EINVAL;

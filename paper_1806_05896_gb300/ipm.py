@@ -33,6 +33,8 @@ EXPORTED = (
     "ipm_profile_smoother", "ipm_profile_read", "ipm_profile_phases", "ipm_strerror", "ipm_last_error",
     "ipm_newton_apply_device", "ipm_precond_apply_device", "ipm_chebyshev_device",
     "ipm_vcycle_device", "ipm_newton_step_device", "ipm_chebyshev_noalloc",
+    "ipm_reset", "ipm_device_bytes", "ipm_server_create", "ipm_server_submit",
+    "ipm_server_wait", "ipm_server_stats", "ipm_server_destroy",
 )
 
 
@@ -66,6 +68,11 @@ class Report(C.Structure):
                 ("kkt_rel", C.c_double), ("xi_p", C.c_double), ("xi_d", C.c_double),
                 ("xi_c", C.c_double), ("mu", C.c_double), ("krylov_relres_max", C.c_double),
                 ("seconds", C.c_double)]
+
+
+class Request(C.Structure):
+    _fields_ = [("grid", Grid), ("pde", Pde), ("alpha", C.c_double), ("beta", C.c_double),
+                ("bounds", Bounds), ("yd", C.POINTER(C.c_double)), ("opt", Options)]
 
 
 class IpmError(RuntimeError):
@@ -118,6 +125,16 @@ def load() -> C.CDLL:
     lib.ipm_newton_step_device.argtypes = [P, C.POINTER(Options), C.POINTER(P), C.c_double, P,
                                            C.POINTER(C.c_int), D]
     lib.ipm_chebyshev_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P]
+    lib.ipm_reset.argtypes = [P, C.c_double, C.c_double, C.POINTER(Bounds)]
+    lib.ipm_device_bytes.argtypes = [P]
+    lib.ipm_device_bytes.restype = C.c_size_t
+    lib.ipm_server_create.argtypes = [C.c_int, C.c_size_t, C.POINTER(P)]
+    lib.ipm_server_submit.argtypes = [P, C.POINTER(Request), C.POINTER(C.c_longlong)]
+    lib.ipm_server_wait.argtypes = [P, C.c_longlong, C.POINTER(Report), D, C.c_size_t, D, D]
+    lib.ipm_server_stats.argtypes = [P, C.POINTER(C.c_size_t), C.POINTER(C.c_int),
+                                     C.POINTER(C.c_longlong)]
+    lib.ipm_server_destroy.argtypes = [P]
+    lib.ipm_server_destroy.restype = None
     _lib = lib
     return lib
 
@@ -159,6 +176,66 @@ def chebyshev_noalloc(dim: int, n: int, steps: int, th_y, b, x, stream: Optional
     if rc != OK:
         raise IpmError(rc, load().ipm_strerror(rc).decode())
     return x
+
+
+class Server:
+    """Native serving loop (worker threads, one CUDA stream each, memory-budget admission)."""
+
+    def __init__(self, workers: int = 4, budget_bytes: int = 64 << 30):
+        self._lib = load()
+        h = C.c_void_p()
+        rc = self._lib.ipm_server_create(workers, budget_bytes, C.byref(h))
+        if rc != OK:
+            raise IpmError(rc, "ipm_server_create failed")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, dim, n, alpha, beta, ua, ub, yd, ya=-math.inf, yb=math.inf, kind="poisson",
+               eps=1.0, options: Optional[Options] = None, **kw) -> int:
+        o = options if options is not None else default_options(**kw)
+        yd = np.ascontiguousarray(np.asarray(yd, dtype=np.float64).reshape(-1))
+        rq = Request(Grid(dim, (C.c_int * 3)(n, n, n if dim == 3 else 0)),
+                     Pde(POISSON if kind == "poisson" else CONVDIFF_SUPG, eps, 0), alpha, beta,
+                     Bounds(ua, ub, ya, yb, None, None, None, None),
+                     yd.ctypes.data_as(C.POINTER(C.c_double)), o)
+        t = C.c_longlong()
+        rc = self._lib.ipm_server_submit(self._h, C.byref(rq), C.byref(t))
+        if rc != OK:
+            raise IpmError(rc, self._lib.ipm_strerror(rc).decode())
+        self._keep[t.value] = yd.size
+        return t.value
+
+    def wait(self, ticket: int):
+        """(report dict, control as a flat array, latency s, queue time s)."""
+        nn = self._keep.pop(ticket)
+        u = np.empty(nn)
+        r = Report()
+        lat = C.c_double()
+        q = C.c_double()
+        rc = self._lib.ipm_server_wait(self._h, ticket, C.byref(r),
+                                       u.ctypes.data_as(C.POINTER(C.c_double)), nn, C.byref(lat),
+                                       C.byref(q))
+        if rc not in (OK, ENOTCONV):
+            raise IpmError(rc, self._lib.ipm_strerror(rc).decode())
+        return {f: getattr(r, f) for f, _ in Report._fields_}, u, lat.value, q.value
+
+    def stats(self):
+        b = C.c_size_t()
+        ns = C.c_int()
+        done = C.c_longlong()
+        self._lib.ipm_server_stats(self._h, C.byref(b), C.byref(ns), C.byref(done))
+        return dict(bytes_in_use=b.value, solvers=ns.value, completed=done.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ipm_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Solver:
@@ -214,6 +291,13 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+    def reset(self, alpha: float, beta: float, ua, ub, ya=-math.inf, yb=math.inf):
+        b = Bounds(ua, ub, ya, yb, None, None, None, None)
+        self._check(self._lib.ipm_reset(self._h, alpha, beta, C.byref(b)))
+
+    def device_bytes(self) -> int:
+        return int(self._lib.ipm_device_bytes(self._h))
 
     def set_stream(self, stream_handle: Optional[int]):
         self._check(self._lib.ipm_set_stream(self._h, stream_handle))
