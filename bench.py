@@ -176,6 +176,8 @@ def run_ours(args, rank, world):
     stream = torch.cuda.Stream()
     # one solver per sweep cell owned by this rank, inputs resident in HBM
     cells = [c for c in range(9) if c % world == rank] or [rank % 9]
+    if args.cells:  # fewer solvers (smaller device footprint, e.g. for profiler captures)
+        cells = cells[:args.cells]
     solvers, yds, yd_host = {}, {}, {}
     for c in cells:
         wl = W.workload_c2(n=n, cell=c)
@@ -398,6 +400,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--legs", default="all", choices=["all", "mixed"])
     ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--cells", type=int, default=0, help="sweep cells per rank (0 = all nine)")
     ap.add_argument("--serve-requests", type=int, default=48)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

@@ -105,7 +105,9 @@ typedef struct {
   int mu_rule;     /* 0: mu <- sigma mu (Algorithm A.1); 1: mu <- sigma * mean complementarity product */
   int kernel_flags; /* 0: fastest kernels; bit 0: per-sweep multigrid/Chebyshev kernels instead of
                        the fused 2D ones; bit 1: no CUDA-graph replay of Krylov iterations;
-                       bits 2 / 3: on the mixed path keep the Chebyshev / multigrid stage in FP64 */
+                       bits 2 / 3: on the mixed path keep the Chebyshev / multigrid stage in FP64;
+                       bit 4: mixed multigrid on the 2D Poisson operator takes its finest-level
+                       outer residual in FP64 instead of float-float arithmetic */
 } ipm_options;
 
 typedef struct {
@@ -244,7 +246,10 @@ int ipm_chebyshev_device(ipm_solver* s, int steps, const double* theta_y, const 
                          double* x);
 
 /* x = V-cycle approximation of (L + diag(m))^{-1} b (transpose = 1: (L^T + diag(m))^{-1}),
- * `cycles` V-cycles from x = 0 with the options' smoothing counts, FP64. m, b, x: nodal. */
+ * `vcycles` V-cycles from x = 0 with the options' smoothing counts. m, b, x: nodal.
+ * FP64 unless opt->precision is IPM_PREC_MIXED: then the cycles run in FP32 on the
+ * correction equation with an FP64 residual and iterate on the finest level, as inside
+ * the mixed-precision preconditioner. */
 int ipm_vcycle_device(ipm_solver* s, const ipm_options* opt, int transpose, const double* m,
                       const double* b, double* x);
 

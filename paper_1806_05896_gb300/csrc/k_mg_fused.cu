@@ -12,6 +12,8 @@
 //
 // A V-cycle on a 1025^2 grid thus takes 2 launches per level above the coarse
 // block plus one, instead of about 14 per level.
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace {
@@ -184,6 +186,213 @@ __global__ void __launch_bounds__(512) k_mg2_prolong_post(GridDesc g, GridDesc g
 }
 
 // ---------------------------------------------------------------------------
+// Register-blocked FP32 tile kernels (same cycle pieces and arithmetic as the two
+// kernels above, laid out for the shared-memory pipe).
+//
+// Thread (lane, warp w) owns the tile nodes in columns 1 + lane + 32c (c < CX) and rows
+// 1 + wK + r (r < K). The right-hand side, the diagonal m and the Jacobi weight of its
+// nodes stay in registers for the whole launch; a sweep slides a three-row window down
+// each owned column, so a node costs 3(K+2)/K shared loads and one store per sweep
+// instead of twelve loads. Every sweep updates all nodes but the tile's outer ring: after
+// sweep s the values within s nodes of the ring differ from the global sweep, and only
+// nodes at least nu nodes inside (nu + 1 for the residual) are used afterwards.
+// Tiles start at the first interior node, so ceil((n - 2) / T) tiles cover a direction.
+// Nodes outside the domain carry zero weight and stay zero.
+// ---------------------------------------------------------------------------
+template <int TX, int TY, int H, int NW>
+struct RBShape {
+  static constexpr int SX = TX + 2 * H, SY = TY + 2 * H;
+  static constexpr int CX = (SX - 2 + 31) / 32;
+  static constexpr int K = (SY - 2 + NW - 1) / NW;
+  static_assert(K * (NW - 1) < SY - 2, "every warp owns at least one row");
+  static_assert(TX % 2 == 0 && TY % 2 == 0, "tiles own whole coarse cells");
+  static constexpr size_t smem = 2 * (size_t)SX * SY * sizeof(float);
+};
+
+enum { kRBSweep = 0, kRBSweepOut = 1, kRBResidual = 2 };
+constexpr int kRBSweeps = 5;  // sweeps per launch the register-blocked kernels are built for
+
+// x into both tile buffers (ring by all threads, owned nodes by their owner) and the
+// owned nodes' b, m, omega / diag into registers; load_x(gx, gy) gives x at an interior node
+template <int TX, int TY, int H, int NW, typename LoadX>
+IPM_D void rb_load(const GridDesc& g, int X0, int Y0, const float* __restrict__ b,
+                   const float* __restrict__ m, float omega, const LoadX& load_x, float* cur,
+                   float* nxt, float (&rb)[RBShape<TX, TY, H, NW>::CX][RBShape<TX, TY, H, NW>::K],
+                   float (&rm)[RBShape<TX, TY, H, NW>::CX][RBShape<TX, TY, H, NW>::K],
+                   float (&rj)[RBShape<TX, TY, H, NW>::CX][RBShape<TX, TY, H, NW>::K]) {
+  using S = RBShape<TX, TY, H, NW>;
+  constexpr int SX = S::SX, SY = S::SY;
+  const int n = g.n, p = g.pitch;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < 2 * SX + 2 * (SY - 2); t += NW * 32) {
+    int lx, ly;
+    if (t < 2 * SX) {
+      lx = t < SX ? t : t - SX;
+      ly = t < SX ? 0 : SY - 1;
+    } else {
+      const int u = t - 2 * SX;
+      ly = 1 + (u >> 1);
+      lx = (u & 1) ? SX - 1 : 0;
+    }
+    const int gx = X0 - H + lx, gy = Y0 - H + ly;
+    const float v = inside<float>(gx, gy, n) ? load_x(gx, gy) : 0.f;
+    cur[ly * SX + lx] = v;
+    nxt[ly * SX + lx] = v;
+  }
+#pragma unroll
+  for (int c = 0; c < S::CX; ++c) {
+    const int lx = 1 + lane + 32 * c;
+#pragma unroll
+    for (int r = 0; r < S::K; ++r) {
+      const int ly = 1 + w * S::K + r;
+      const int gx = X0 - H + lx, gy = Y0 - H + ly;
+      float bb = 0.f, mm = 0.f, jj = 0.f;
+      if (lx <= SX - 2 && ly <= SY - 2) {
+        float xx = 0.f;
+        if (inside<float>(gx, gy, n)) {
+          const long long i = (long long)gy * p + gx;
+          bb = b[i];
+          mm = m[i];
+          jj = omega / (float(8.0 / 3.0) + mm);
+          xx = load_x(gx, gy);
+        }
+        cur[ly * SX + lx] = xx;
+      }
+      rb[c][r] = bb;
+      rm[c][r] = mm;
+      rj[c][r] = jj;
+    }
+  }
+}
+
+// one pass over the owned nodes: a Jacobi sweep into nxt (kRBSweep) or into xout for the
+// nodes of the tile proper (kRBSweepOut), or the residual b - A x into nxt with x of the
+// tile proper copied to xout (kRBResidual)
+template <int MODE, int TX, int TY, int H, int NW>
+IPM_D void rb_pass(const float* __restrict__ cur, float* __restrict__ nxt,
+                   const float (&rb)[RBShape<TX, TY, H, NW>::CX][RBShape<TX, TY, H, NW>::K],
+                   const float (&rm)[RBShape<TX, TY, H, NW>::CX][RBShape<TX, TY, H, NW>::K],
+                   const float (&rj)[RBShape<TX, TY, H, NW>::CX][RBShape<TX, TY, H, NW>::K],
+                   float* __restrict__ xout, const GridDesc& g, int X0, int Y0) {
+  using S = RBShape<TX, TY, H, NW>;
+  constexpr int SX = S::SX, SY = S::SY, K = S::K;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int ly0 = 1 + w * K;
+#pragma unroll
+  for (int c = 0; c < S::CX; ++c) {
+    const int lx = 1 + lane + 32 * c;
+    if (lx > SX - 2) continue;
+    const float* col = cur + lx;
+    const float* q = col + (ly0 - 1) * SX;
+    float hp = (q[-1] + q[0]) + q[1];
+    q = col + ly0 * SX;
+    float xc = q[0];
+    float hc = (q[-1] + xc) + q[1];
+    const int gx = X0 - H + lx;
+    const bool out_col = MODE != kRBSweep && lx >= H && lx < H + TX && gx <= g.n - 2;
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+      const int ly = ly0 + r;
+      if (K * NW > SY - 2 && ly > SY - 2) break;
+      q = col + (ly + 1) * SX;
+      const float xn = q[0];
+      const float hn = (q[-1] + xn) + q[1];
+      const float box = (hp + hc) + hn;
+      const float ax = (3.0f * xc - box * float(1.0 / 3.0)) + rm[c][r] * xc;
+      const int gy = Y0 - H + ly;
+      const bool out = out_col && ly >= H && ly < H + TY && gy <= g.n - 2;
+      if (MODE == kRBResidual) {
+        nxt[ly * SX + lx] = rj[c][r] != 0.f ? rb[c][r] - ax : 0.f;
+        if (out) xout[(long long)gy * g.pitch + gx] = xc;
+      } else {
+        const float v = xc + rj[c][r] * (rb[c][r] - ax);
+        if (MODE == kRBSweep) nxt[ly * SX + lx] = v;
+        else if (out) xout[(long long)gy * g.pitch + gx] = v;
+      }
+      hp = hc;
+      hc = hn;
+      xc = xn;
+    }
+  }
+}
+
+template <int TX, int TY, int NU, int NW>
+__global__ void __launch_bounds__(NW * 32) k_mg2_pre_restrict_rb(GridDesc g, GridDesc gc,
+                                                                 const float* __restrict__ xin,
+                                                                 float* __restrict__ xout,
+                                                                 const float* __restrict__ b,
+                                                                 const float* __restrict__ m,
+                                                                 float* __restrict__ bc,
+                                                                 float omega, int zero_init) {
+  constexpr int H = NU + 2;
+  using S = RBShape<TX, TY, H, NW>;
+  constexpr int SX = S::SX;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* cur = reinterpret_cast<float*>(smem_raw);
+  float* nxt = cur + SX * S::SY;
+  const int X0 = 1 + blockIdx.x * TX, Y0 = 1 + blockIdx.y * TY;
+  const long long p = g.pitch;
+  float rb[S::CX][S::K], rm[S::CX][S::K], rj[S::CX][S::K];
+  auto load_x = [&](int gx, int gy) { return zero_init ? 0.f : xin[(long long)gy * p + gx]; };
+  rb_load<TX, TY, H, NW>(g, X0, Y0, b, m, omega, load_x, cur, nxt, rb, rm, rj);
+  __syncthreads();
+#pragma unroll 1
+  for (int s = 0; s < NU; ++s) {
+    rb_pass<kRBSweep, TX, TY, H, NW>(cur, nxt, rb, rm, rj, nullptr, g, X0, Y0);
+    __syncthreads();
+    float* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  rb_pass<kRBResidual, TX, TY, H, NW>(cur, nxt, rb, rm, rj, xout, g, X0, Y0);
+  __syncthreads();
+  // full weighting onto the coarse nodes I with 2I in [X0, X0 + TX) (X0 is odd)
+  const int nc = gc.n;
+  for (int t = threadIdx.x; t < (TX / 2) * (TY / 2); t += NW * 32) {
+    const int I = (X0 + 1) / 2 + t % (TX / 2), J = (Y0 + 1) / 2 + t / (TX / 2);
+    if (I > nc - 2 || J > nc - 2) continue;
+    const int i = (2 * J - Y0 + H) * SX + (2 * I - X0 + H);
+    const float r0 = 0.5f * nxt[i - SX - 1] + nxt[i - SX] + 0.5f * nxt[i - SX + 1];
+    const float r1 = 0.5f * nxt[i - 1] + nxt[i] + 0.5f * nxt[i + 1];
+    const float r2 = 0.5f * nxt[i + SX - 1] + nxt[i + SX] + 0.5f * nxt[i + SX + 1];
+    bc[(long long)J * gc.pitch + I] = 0.5f * r0 + r1 + 0.5f * r2;
+  }
+}
+
+template <int TX, int TY, int NU, int NW>
+__global__ void __launch_bounds__(NW * 32) k_mg2_prolong_post_rb(GridDesc g, GridDesc gc,
+                                                                 const float* __restrict__ xin,
+                                                                 const float* __restrict__ xc,
+                                                                 float* __restrict__ xout,
+                                                                 const float* __restrict__ b,
+                                                                 const float* __restrict__ m,
+                                                                 float omega) {
+  constexpr int H = NU;
+  using S = RBShape<TX, TY, H, NW>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* cur = reinterpret_cast<float*>(smem_raw);
+  float* nxt = cur + S::SX * S::SY;
+  const int X0 = 1 + blockIdx.x * TX, Y0 = 1 + blockIdx.y * TY;
+  const long long p = g.pitch;
+  const int cp = gc.pitch;
+  float rb[S::CX][S::K], rm[S::CX][S::K], rj[S::CX][S::K];
+  auto load_x = [&](int gx, int gy) {
+    return xin[(long long)gy * p + gx] + prolong_at(xc, cp, gx, gy);
+  };
+  rb_load<TX, TY, H, NW>(g, X0, Y0, b, m, omega, load_x, cur, nxt, rb, rm, rj);
+  __syncthreads();
+#pragma unroll 1
+  for (int s = 0; s < NU - 1; ++s) {
+    rb_pass<kRBSweep, TX, TY, H, NW>(cur, nxt, rb, rm, rj, nullptr, g, X0, Y0);
+    __syncthreads();
+    float* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  rb_pass<kRBSweepOut, TX, TY, H, NW>(cur, nxt, rb, rm, rj, xout, g, X0, Y0);
+}
+
+// ---------------------------------------------------------------------------
 // One CTA, all coarse levels in shared memory (dense n x n per level).
 // ---------------------------------------------------------------------------
 // one damped-Jacobi sweep over the interior of an n x n level (threads as 32 x 32 grid)
@@ -205,84 +414,91 @@ __global__ void __launch_bounds__(1024) k_mg2_coarse(MGCoarse<T> cl, const T* __
                                                      int nu_post, int load_x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* base = reinterpret_cast<T*>(smem_raw);
-  T* X0[kMaxCoarse];
-  T* X1[kMaxCoarse];
-  T* B[kMaxCoarse];
-  T* R[kMaxCoarse];
-  T* Mm[kMaxCoarse];
-  T* Jv[kMaxCoarse];
-  int off = 0;
-  for (int l = 0; l < cl.nl; ++l) {
-    int s = cl.n[l] * cl.n[l];
-    X0[l] = base + off;
-    X1[l] = X0[l] + s;
-    B[l] = X1[l] + s;
-    R[l] = B[l] + s;
-    Mm[l] = R[l] + s;
-    Jv[l] = Mm[l] + s;
-    off += 6 * s;
+  // per-level size and offset of the six arrays (x0, x1, b, r, m, jinv) in a shared table,
+  // and the current-iterate parity of every level as a register bit mask: indexing
+  // per-thread arrays by the runtime level index would put them in local memory
+  __shared__ int s_n[kMaxCoarse], s_off[kMaxCoarse];
+  if (threadIdx.x == 0) {
+    int off = 0;
+    for (int l = 0; l < cl.nl; ++l) {
+      s_n[l] = cl.n[l];
+      s_off[l] = off;
+      off += 6 * cl.n[l] * cl.n[l];
+    }
   }
+  __syncthreads();
+  const int total = s_off[cl.nl - 1] + 6 * s_n[cl.nl - 1] * s_n[cl.nl - 1];
+  auto arr = [&](int l, int a) { return base + s_off[l] + a * s_n[l] * s_n[l]; };
+  enum { AX0 = 0, AX1 = 1, AB = 2, AR = 3, AM = 4, AJ = 5 };
   // zero everything, then load b (top level) and m (all levels), interior entries
-  for (int t = threadIdx.x; t < off; t += blockDim.x) base[t] = T(0);
+  for (int t = threadIdx.x; t < total; t += blockDim.x) base[t] = T(0);
   __syncthreads();
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
   for (int l = 0; l < cl.nl; ++l) {
-    int n = cl.n[l];
+    const int n = s_n[l];
+    T* Ml = arr(l, AM);
+    T* Jl = arr(l, AJ);
+    const T* mg = cl.m[l];
+    const long long pl = cl.pitch[l];
     for (int iy = 1 + ty; iy < n - 1; iy += ny)
       for (int ix = 1 + tx; ix < n - 1; ix += 32) {
-        T mm = cl.m[l][(long long)iy * cl.pitch[l] + ix];
-        Mm[l][iy * n + ix] = mm;
-        Jv[l][iy * n + ix] = omega / (T(8.0 / 3.0) + mm);
-        if (l == 0) B[0][iy * n + ix] = btop[(long long)iy * cl.pitch[0] + ix];
-        if (l == 0 && load_x) X0[0][iy * n + ix] = xtop[(long long)iy * cl.pitch[0] + ix];
+        T mm = mg[(long long)iy * pl + ix];
+        Ml[iy * n + ix] = mm;
+        Jl[iy * n + ix] = omega / (T(8.0 / 3.0) + mm);
+        if (l == 0) arr(0, AB)[iy * n + ix] = btop[(long long)iy * cl.pitch[0] + ix];
+        if (l == 0 && load_x) arr(0, AX0)[iy * n + ix] = xtop[(long long)iy * cl.pitch[0] + ix];
       }
   }
   __syncthreads();
-  int cur[kMaxCoarse];
-  for (int l = 0; l < cl.nl; ++l) cur[l] = 0;
+  unsigned cur = 0;  // bit l: level l's current iterate is x1
+  auto xcur = [&](int l) { return arr(l, ((cur >> l) & 1u) ? AX1 : AX0); };
+  auto xnxt = [&](int l) { return arr(l, ((cur >> l) & 1u) ? AX0 : AX1); };
   const int L = cl.nl - 1;
   for (int l = 0; l < L; ++l) {
-    int n = cl.n[l];
+    const int n = s_n[l];
+    const T* Bl = arr(l, AB);
+    const T* Ml = arr(l, AM);
+    const T* Jl = arr(l, AJ);
+    T* Rl = arr(l, AR);
     for (int s = 0; s < nu_pre; ++s) {
-      T* c = cur[l] ? X1[l] : X0[l];
-      T* nx = cur[l] ? X0[l] : X1[l];
-      cta_sweep(c, nx, B[l], Mm[l], Jv[l], n, s == 0 && !(l == 0 && load_x));
-      cur[l] ^= 1;
+      cta_sweep(xcur(l), xnxt(l), Bl, Ml, Jl, n, s == 0 && !(l == 0 && load_x));
+      cur ^= 1u << l;
       __syncthreads();
     }
     {
-      T* c = cur[l] ? X1[l] : X0[l];
+      const T* c = xcur(l);
       for (int iy = 1 + ty; iy < n - 1; iy += ny)
         for (int ix = 1 + tx; ix < n - 1; ix += 32) {
           const int i = iy * n + ix;
-          R[l][i] = B[l][i] - apply_A(c, i, n, Mm[l][i]);
+          Rl[i] = Bl[i] - apply_A(c, i, n, Ml[i]);
         }
     }
     __syncthreads();
     {
-      int nc = cl.n[l + 1];
+      const int nc = s_n[l + 1];
+      T* Bc = arr(l + 1, AB);
       for (int J = 1 + ty; J < nc - 1; J += ny)
         for (int I = 1 + tx; I < nc - 1; I += 32) {
-          int i = (2 * J) * n + 2 * I;
-          const T* r = R[l];
+          const int i = (2 * J) * n + 2 * I;
+          const T* r = Rl;
           T r0 = T(0.5) * r[i - n - 1] + r[i - n] + T(0.5) * r[i - n + 1];
           T r1 = T(0.5) * r[i - 1] + r[i] + T(0.5) * r[i + 1];
           T r2 = T(0.5) * r[i + n - 1] + r[i + n] + T(0.5) * r[i + n + 1];
-          B[l + 1][J * nc + I] = T(0.5) * r0 + r1 + T(0.5) * r2;
+          Bc[J * nc + I] = T(0.5) * r0 + r1 + T(0.5) * r2;
         }
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {  // coarsest grid: 3 nodes per direction, one unknown
-    int i = 1 * 3 + 1;
-    X0[L][i] = B[L][i] / (T(8.0 / 3.0) + Mm[L][i]);
-    cur[L] = 0;
+    const int i = 1 * 3 + 1;
+    arr(L, AX0)[i] = arr(L, AB)[i] / (T(8.0 / 3.0) + arr(L, AM)[i]);
   }
+  cur &= ~(1u << L);
   __syncthreads();
   for (int l = L - 1; l >= 0; --l) {
-    int n = cl.n[l], nc = cl.n[l + 1];
-    T* c = cur[l] ? X1[l] : X0[l];
-    const T* xcs = cur[l + 1] ? X1[l + 1] : X0[l + 1];
+    const int n = s_n[l], nc = s_n[l + 1];
+    T* c = xcur(l);
+    const T* xcs = xcur(l + 1);
     const bool wipe = nu_pre == 0 && !(l == 0 && load_x);  // x never written on this level
     for (int iy = 1 + ty; iy < n - 1; iy += ny)
       for (int ix = 1 + tx; ix < n - 1; ix += 32) {
@@ -290,17 +506,18 @@ __global__ void __launch_bounds__(1024) k_mg2_coarse(MGCoarse<T> cl, const T* __
         c[iy * n + ix] = base_v + prolong_at(xcs, nc, ix, iy);
       }
     __syncthreads();
+    const T* Bl = arr(l, AB);
+    const T* Ml = arr(l, AM);
+    const T* Jl = arr(l, AJ);
     for (int s = 0; s < nu_post; ++s) {
-      T* cc = cur[l] ? X1[l] : X0[l];
-      T* nx = cur[l] ? X0[l] : X1[l];
-      cta_sweep(cc, nx, B[l], Mm[l], Jv[l], n, 0);
-      cur[l] ^= 1;
+      cta_sweep(xcur(l), xnxt(l), Bl, Ml, Jl, n, 0);
+      cur ^= 1u << l;
       __syncthreads();
     }
   }
   {
-    int n = cl.n[0];
-    const T* c = cur[0] ? X1[0] : X0[0];
+    const int n = s_n[0];
+    const T* c = xcur(0);
     for (int iy = 1 + ty; iy < n - 1; iy += ny)
       for (int ix = 1 + tx; ix < n - 1; ix += 32) xtop[(long long)iy * cl.pitch[0] + ix] = c[iy * n + ix];
   }
@@ -343,10 +560,46 @@ void pre_restrict_tiles(const GridDesc& g, const GridDesc& gc, const T* xin, T* 
                                                           zero_init);
 }
 
+template <int TX, int TY, int NW>
+void pre_restrict_rb(const GridDesc& g, const GridDesc& gc, const float* xin, float* xout,
+                     const float* b, const float* m, float* bc, double omega, int zero_init,
+                     cudaStream_t s) {
+  constexpr int NU = kRBSweeps;
+  static size_t set_to = 0;
+  const size_t sm = RBShape<TX, TY, NU + 2, NW>::smem;
+  ensure_smem_attr((const void*)k_mg2_pre_restrict_rb<TX, TY, NU, NW>, sm, set_to);
+  dim3 grid((g.n - 2 + TX - 1) / TX, (g.n - 2 + TY - 1) / TY);
+  count_launches(1);
+  k_mg2_pre_restrict_rb<TX, TY, NU, NW><<<grid, NW * 32, sm, s>>>(g, gc, xin, xout, b, m, bc,
+                                                                 (float)omega, zero_init);
+}
+
+template <int TX, int TY, int NW>
+void prolong_post_rb(const GridDesc& g, const GridDesc& gc, const float* xin, const float* xc,
+                     float* xout, const float* b, const float* m, double omega, cudaStream_t s) {
+  constexpr int NU = kRBSweeps;
+  static size_t set_to = 0;
+  const size_t sm = RBShape<TX, TY, NU, NW>::smem;
+  ensure_smem_attr((const void*)k_mg2_prolong_post_rb<TX, TY, NU, NW>, sm, set_to);
+  dim3 grid((g.n - 2 + TX - 1) / TX, (g.n - 2 + TY - 1) / TY);
+  count_launches(1);
+  k_mg2_prolong_post_rb<TX, TY, NU, NW><<<grid, NW * 32, sm, s>>>(g, gc, xin, xc, xout, b, m,
+                                                                 (float)omega);
+}
+
 template <typename T>
 void launch_mg2_pre_restrict(const GridDesc& g, const GridDesc& gc, const T* xin, T* xout,
                              const T* b, const T* m, T* bc, double omega, int nu, int zero_init,
                              cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (nu == kRBSweeps) {
+      // tile shapes from a timing sweep on GB300 (52 + 12 and 20 + 12 halo columns fill
+      // whole 32-lane column groups)
+      if (g.n > 513) pre_restrict_rb<52, 52, 16>(g, gc, xin, xout, b, m, bc, omega, zero_init, s);
+      else pre_restrict_rb<20, 32, 8>(g, gc, xin, xout, b, m, bc, omega, zero_init, s);
+      return;
+    }
+  }
   if (g.n >= 513)
     pre_restrict_tiles<T, 64, 32>(g, gc, xin, xout, b, m, bc, omega, nu, zero_init, 512, s);
   else
@@ -370,6 +623,13 @@ template <typename T>
 void launch_mg2_prolong_post(const GridDesc& g, const GridDesc& gc, const T* xin, const T* xc,
                              T* xout, const T* b, const T* m, double omega, int nu,
                              cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (nu == kRBSweeps) {
+      if (g.n > 513) prolong_post_rb<56, 32, 8>(g, gc, xin, xc, xout, b, m, omega, s);
+      else prolong_post_rb<24, 24, 8>(g, gc, xin, xc, xout, b, m, omega, s);
+      return;
+    }
+  }
   if (g.n >= 513) prolong_post_tiles<T, 64, 32>(g, gc, xin, xc, xout, b, m, omega, nu, 512, s);
   else prolong_post_tiles<T, 32, 16>(g, gc, xin, xc, xout, b, m, omega, nu, 256, s);
 }
@@ -487,12 +747,176 @@ __global__ void __launch_bounds__(512) k_cheb2_block(GridDesc g, ChebSteps cs, c
   }
 }
 
+// Register-blocked FP32 form of k_cheb2_block (same recurrence and arithmetic): the
+// owner of a node keeps its b, Theta_y, 1 / (D_M + Theta_y) and previous iterate in
+// registers, the current iterate is exchanged through shared memory. Nodes outside the
+// domain carry a zero inverse diagonal and stay zero.
+template <int TX, int TY, int NS, int NW>
+__global__ void __launch_bounds__(NW * 32) k_cheb2_rb(GridDesc g, ChebSteps cs,
+                                                      const double* __restrict__ b,
+                                                      const float* __restrict__ thy,
+                                                      const float* xc_in, const float* xp_in,
+                                                      float* xc_out, float* xp_out,
+                                                      double* final_out, int first) {
+  constexpr int H = NS;
+  using S = RBShape<TX, TY, H, NW>;
+  constexpr int SX = S::SX, SY = S::SY, CX = S::CX, K = S::K;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* cur = reinterpret_cast<float*>(smem_raw);
+  float* nxt = cur + SX * SY;
+  const int X0 = 1 + blockIdx.x * TX, Y0 = 1 + blockIdx.y * TY;
+  const int n = g.n;
+  const long long p = g.pitch;
+  const float dM = (float)cs.dM, gam = (float)cs.gamma, ms = (float)cs.mscale;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < 2 * SX + 2 * (SY - 2); t += NW * 32) {
+    int lx, ly;
+    if (t < 2 * SX) {
+      lx = t < SX ? t : t - SX;
+      ly = t < SX ? 0 : SY - 1;
+    } else {
+      const int u = t - 2 * SX;
+      ly = 1 + (u >> 1);
+      lx = (u & 1) ? SX - 1 : 0;
+    }
+    const int gx = X0 - H + lx, gy = Y0 - H + ly;
+    float v = 0.f;
+    if (inside<float>(gx, gy, n)) {
+      const long long c = (long long)gy * p + gx;
+      if (first) v = gam * (float)b[c] * (1.0f / (dM + thy[c]));
+      else v = xc_in[c];
+    }
+    cur[ly * SX + lx] = v;
+    nxt[ly * SX + lx] = v;
+  }
+  float rb[CX][K], rt[CX][K], ri[CX][K], rp[CX][K];
+#pragma unroll
+  for (int c = 0; c < CX; ++c) {
+    const int lx = 1 + lane + 32 * c;
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+      const int ly = 1 + w * K + r;
+      const int gx = X0 - H + lx, gy = Y0 - H + ly;
+      float bb = 0.f, th = 0.f, iv = 0.f, xp = 0.f;
+      if (lx <= SX - 2 && ly <= SY - 2) {
+        float x = 0.f;
+        if (inside<float>(gx, gy, n)) {
+          const long long i = (long long)gy * p + gx;
+          bb = (float)b[i];
+          th = thy[i];
+          iv = 1.0f / (dM + th);
+          if (first) {
+            x = gam * bb * iv;
+          } else {
+            x = xc_in[i];
+            xp = xp_in[i];
+          }
+        }
+        cur[ly * SX + lx] = x;
+      }
+      rb[c][r] = bb;
+      rt[c][r] = th;
+      ri[c][r] = iv;
+      rp[c][r] = xp;
+    }
+  }
+  __syncthreads();
+  const int ly0 = 1 + w * K;
+#pragma unroll
+  for (int s = 1; s <= NS; ++s) {
+    const float om = (float)cs.omega[s - 1];
+    const float og = om * gam;
+    const bool last = s == NS;
+#pragma unroll
+    for (int c = 0; c < CX; ++c) {
+      const int lx = 1 + lane + 32 * c;
+      if (lx > SX - 2) continue;
+      const float* col = cur + lx;
+      const float* q = col + (ly0 - 1) * SX;
+      float hp = (q[-1] + 4.0f * q[0]) + q[1];
+      q = col + ly0 * SX;
+      float xc = q[0];
+      float hc = (q[-1] + 4.0f * xc) + q[1];
+      const int gx = X0 - H + lx;
+      const bool out_col = lx >= H && lx < H + TX && gx <= n - 2;
+#pragma unroll
+      for (int r = 0; r < K; ++r) {
+        const int ly = ly0 + r;
+        if (K * NW > SY - 2 && ly > SY - 2) break;
+        q = col + (ly + 1) * SX;
+        const float xn = q[0];
+        const float hn = (q[-1] + 4.0f * xn) + q[1];
+        const float ax = ms * ((hp + 4.0f * hc) + hn) + rt[c][r] * xc;
+        const float v = xc + (om - 1.0f) * (xc - rp[c][r]) + og * (rb[c][r] - ax) * ri[c][r];
+        if (last) {
+          const int gy = Y0 - H + ly;
+          if (out_col && ly >= H && ly < H + TY && gy <= n - 2) {
+            const long long i = (long long)gy * p + gx;
+            if (final_out) {
+              final_out[i] = (double)v;
+            } else {
+              xc_out[i] = v;
+              xp_out[i] = xc;
+            }
+          }
+        } else {
+          nxt[ly * SX + lx] = v;
+        }
+        rp[c][r] = xc;
+        hp = hc;
+        hc = hn;
+        xc = xn;
+      }
+    }
+    if (!last) {
+      __syncthreads();
+      float* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+  }
+}
+
+template <int TX, int TY, int NS, int NW>
+void cheb2_rb(const GridDesc& g, const ChebSteps& cs, const double* b, const float* thy,
+              const float* xc_in, const float* xp_in, float* xc_out, float* xp_out,
+              double* final_out, int first, cudaStream_t s) {
+  static size_t set_to = 0;
+  const size_t sm = RBShape<TX, TY, NS, NW>::smem;
+  ensure_smem_attr((const void*)k_cheb2_rb<TX, TY, NS, NW>, sm, set_to);
+  dim3 grid((g.n - 2 + TX - 1) / TX, (g.n - 2 + TY - 1) / TY);
+  count_launches(1);
+  k_cheb2_rb<TX, TY, NS, NW><<<grid, NW * 32, sm, s>>>(g, cs, b, thy, xc_in, xp_in, xc_out,
+                                                        xp_out, final_out, first);
+}
+
+// FP32 iterates: register-blocked kernels for blocks of 4 or 5 steps; true when launched
+template <int NS>
+bool cheb2_rb_dispatch(const GridDesc& g, const ChebSteps& cs, const double* b, const float* thy,
+                       const float* xc_in, const float* xp_in, float* xc_out, float* xp_out,
+                       double* final_out, int first, cudaStream_t s) {
+  if (g.n > 513) cheb2_rb<56, 32, NS, 8>(g, cs, b, thy, xc_in, xp_in, xc_out, xp_out, final_out, first, s);
+  else cheb2_rb<24, 24, NS, 8>(g, cs, b, thy, xc_in, xp_in, xc_out, xp_out, final_out, first, s);
+  return true;
+}
+
 }  // namespace
 
 template <typename T, typename Ti, typename To>
 void launch_cheb2_block(const GridDesc& g, const ChebSteps& cs, const Ti* b, const T* thy,
                         const T* xc_in, const T* xp_in, T* xc_out, T* xp_out, To* final_out,
                         int first, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value && std::is_same<Ti, double>::value &&
+                std::is_same<To, double>::value) {
+    if (cs.ns == 5) {
+      cheb2_rb_dispatch<5>(g, cs, b, thy, xc_in, xp_in, xc_out, xp_out, final_out, first, s);
+      return;
+    }
+    if (cs.ns == 4) {
+      cheb2_rb_dispatch<4>(g, cs, b, thy, xc_in, xp_in, xc_out, xp_out, final_out, first, s);
+      return;
+    }
+  }
   static size_t set_to = 0;
   size_t sm = 6 * (size_t)(FTX + 2 * cs.ns) * (FTY + 2 * cs.ns) * sizeof(T);
   ensure_smem_attr((const void*)k_cheb2_block<T, Ti, To>, sm, set_to);

@@ -110,6 +110,12 @@ void launch_mg_zero(const GridDesc& g, T* x, cudaStream_t s);
 void launch_mg_outer(const GridDesc& g, OpL L, const double* xprev, const float* e,
                      const double* b, const double* m, double* xnew, float* r32, int transpose,
                      cudaStream_t s);
+// float-float form of the outer step for the 2D Poisson operator (FP32 instruction rates)
+void launch_mg_outer_ff(const GridDesc& g, const float* xh_in, const float* xl_in, const float* e,
+                        const double* b64, float* b3h, float* b3l, const float* m3h,
+                        const float* m3l, float* xh_out, float* xl_out, float* r32, double* out64,
+                        int first, cudaStream_t s);
+void launch_split3_ff(const GridDesc& g, const double* m, float* hi, float* lo, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
 // k_mg_fused.cu (2D Poisson: tiled multi-sweep kernels and a one-CTA coarse cycle)

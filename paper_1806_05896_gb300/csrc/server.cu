@@ -54,7 +54,7 @@ size_t estimate_bytes(const ipm_request& r) {
   const long long nodes = r.grid.dim == 2 ? n * n : n * n * n;
   const long long restart = r.opt.restart > 0 ? r.opt.restart : 50;
   double mg = r.grid.dim == 2 ? 4.0 / 3.0 : 8.0 / 7.0;
-  double fields = 21 + 3 * 4 + 4 + 2 + 3 + 2      // state, data, diagonals, Krylov, buffers
+  double fields = 21 + 3 * 4 + 4 + 2 + 3 + 2 + 4  // state, data, diagonals, Krylov, buffers
                   + 0.5 * 2 + 0.5 * 4               // FP32 diagonals and Chebyshev
                   + mg * (5 * 1.0 + 5 * 0.5)        // FP64 + FP32 multigrid levels
                   + (2 * restart + 1) * 4.0;        // FGMRES V and Z

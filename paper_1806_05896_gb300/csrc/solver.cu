@@ -70,6 +70,10 @@ struct ipm_solver {
   MGHier<double> mg64;
   MGHier<float> mg32;
   double *mgb64 = nullptr, *mgx64[2] = {};  // FP64 right-hand side and iterates of the mixed solve
+  float *mgb3 = nullptr, *mgm3 = nullptr;    // float-float 3b and 3m (high part, then low part)
+  float* mgxf[2] = {};                       // float-float iterates (own buffers: the FP64 ones
+                                             // keep zero boundaries in their own layout)
+  bool ff_outer = true;
   // stored operator per multigrid level (convection-diffusion); empty for Poisson
   std::vector<OpL> lvop;
   double *part = nullptr, *dout = nullptr, *sc = nullptr, *kdev = nullptr;
@@ -318,6 +322,10 @@ struct ipm_solver {
     mgb64 = alloc<double>(f);
     mgx64[0] = alloc<double>(f);
     mgx64[1] = alloc<double>(f);
+    mgb3 = alloc<float>(2 * f);
+    mgxf[0] = alloc<float>(2 * f);
+    mgxf[1] = alloc<float>(2 * f);
+    mgm3 = alloc<float>(2 * f);
     part_rows = std::max<long long>(interior_blocks(g), 8 * kRedBlocks);
     part = alloc<double>(part_rows * 8);
     dout = alloc<double>(64);
@@ -529,10 +537,34 @@ struct ipm_solver {
   // the same operator as `vcycles` cycles from zero. In FP32 alone the finest-level
   // residual of a smooth iterate loses its digits to cancellation in the stiffness
   // stencil (8 x_c - neighbours ~ h^2 x''), which slows the outer Krylov method.
+  // float-float outer residual: 2D Poisson (constant-coefficient stencil) only
+  bool use_ff_outer() const { return ff_outer && g.dim == 2 && lvop.empty(); }
+
+  // FP32 multigrid setup of the mixed path from dg.mh (and its FP32 copy dg.mh32)
+  void mg_setup_mixed() {
+    mg_setup(mg32, dg.mh32);
+    if (use_ff_outer()) launch_split3_ff(g, dg.mh, mgm3, mgm3 + F(), stream);
+  }
+
   void mg_solve_mixed(const double* b64, double* out, int tr, const ipm_options& o) {
     MGLevel<float>& L0 = mg32.lv[0];
     const int cycles = std::max(1, o.vcycles);
     launch_convert<double, float>(g, b64, L0.b, stream);
+    if (use_ff_outer()) {
+      // iterate x as float-float (high part, then low part)
+      const long long f = F();
+      for (int c = 0; c < cycles; ++c) {
+        if (fused_mg()) vcycle_fused(mg32, true, o);
+        else vcycle(mg32, 0, true, tr, o);
+        const float* e = L0.x[mg32.cur[0]];
+        const bool last = c == cycles - 1;
+        float* xin = mgxf[(c + 1) & 1];
+        float* xout = mgxf[c & 1];
+        launch_mg_outer_ff(g, xin, xin + f, e, b64, mgb3, mgb3 + f, mgm3, mgm3 + f, xout, xout + f,
+                           last ? nullptr : L0.b, last ? out : nullptr, c == 0 ? 1 : 0, stream);
+      }
+      return;
+    }
     const double* xprev = nullptr;
     int xb = 0;
     for (int c = 0; c < cycles; ++c) {
@@ -671,7 +703,7 @@ struct ipm_solver {
   }
 
   void setup_precond(const ipm_options& o) {
-    if (o.precision == IPM_PREC_MIXED && !(o.kernel_flags & 8)) mg_setup(mg32, dg.mh32);
+    if (o.precision == IPM_PREC_MIXED && !(o.kernel_flags & 8)) mg_setup_mixed();
     else mg_setup(mg64, dg.mh);
   }
 
@@ -961,6 +993,7 @@ struct ipm_solver {
 
   void apply_flags(const ipm_options& o) {
     fused = (o.kernel_flags & 1) == 0;
+    ff_outer = (o.kernel_flags & 16) == 0;
     nu_fits = o.smooth_pre <= 8 && o.smooth_post <= 8;
     use_graphs = (o.kernel_flags & 2) == 0;
   }
@@ -1329,10 +1362,20 @@ int ipm_vcycle_device(ipm_solver* s, const ipm_options* opt, int tr, const doubl
   return guarded(s, [&] {
     s->apply_flags(o);
     launch_pack(s->g, m, s->dg.mh, 1, s->stream);
-    s->mg_setup(s->mg64, s->dg.mh);
-    launch_pack(s->g, b, s->mg64.lv[0].b, 1, s->stream);
-    double* xr = s->mg_solve(s->mg64, tr, o);
-    launch_unpack(s->g, xr, nullptr, x, s->stream);
+    if (o.precision == IPM_PREC_MIXED) {
+      // the preconditioner's mixed solve: FP32 cycles, FP64 outer residual and iterate
+      launch_convert<double, float>(s->g, s->dg.mh, s->dg.mh32, s->stream);
+      s->mg_setup_mixed();
+      launch_pack(s->g, b, s->mgb64, 1, s->stream);
+      double* xr = s->mg64.lv[0].x[0];
+      s->mg_solve_mixed(s->mgb64, xr, tr, o);
+      launch_unpack(s->g, xr, nullptr, x, s->stream);
+    } else {
+      s->mg_setup(s->mg64, s->dg.mh);
+      launch_pack(s->g, b, s->mg64.lv[0].b, 1, s->stream);
+      double* xr = s->mg_solve(s->mg64, tr, o);
+      launch_unpack(s->g, xr, nullptr, x, s->stream);
+    }
     s->sync();
     return IPM_OK;
   });
