@@ -105,9 +105,13 @@ typedef struct {
   int mu_rule;     /* 0: mu <- sigma mu (Algorithm A.1); 1: mu <- sigma * mean complementarity product */
   int kernel_flags; /* 0: fastest kernels; bit 0: per-sweep multigrid/Chebyshev kernels instead of
                        the fused 2D ones; bit 1: no CUDA-graph replay of Krylov iterations;
-                       bits 2 / 3: on the mixed path keep the Chebyshev / multigrid stage in FP64;
+                       bits 2 / 3: on the mixed path keep the Chebyshev and z-block / the
+                       multigrid stage in FP64;
                        bit 4: mixed multigrid on the 2D Poisson operator takes its finest-level
-                       outer residual in FP64 instead of float-float arithmetic */
+                       outer residual in FP64 instead of float-float arithmetic;
+                       bit 5: mixed FGMRES keeps its Arnoldi basis in FP64 instead of
+                       float-float (orthogonalisation and norms); bit 6: with a float-float
+                       basis, apply P_T to its FP64 conversion instead of in float-float */
 } ipm_options;
 
 typedef struct {

@@ -220,3 +220,43 @@ IPM_D double block_min(double v, double* sh) {
   __syncthreads();
   return r;
 }
+
+// ---------------------------------------------------------------------------
+// Float-float (double-single) arithmetic: a value is the unevaluated sum h + l of two
+// floats with |l| <= ulp(h) / 2. Error-free transformations: TwoSum (Knuth), FastTwoSum
+// (Dekker, |a| >= |b|), and the exact product error of a fused multiply-add. Additions
+// use the cheap form (one TwoSum plus the low parts), whose error is about
+// 2^-46 (|a| + |b|). Used where FP64 arithmetic would bound a kernel: this GPU's FP64
+// rate (and its FP64 <-> FP32 conversion rate) is about 1/70 of its FP32 rate. The _rn
+// intrinsics keep the compiler from contracting the transformations into fused
+// multiply-adds.
+// ---------------------------------------------------------------------------
+struct FF {
+  float h, l;
+};
+IPM_D FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+IPM_D FF ff_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+IPM_D FF ff_add(FF a, FF b) {
+  FF s = ff_two_sum(a.h, b.h);
+  return ff_fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+IPM_D FF ff_neg(FF a) { return {-a.h, -a.l}; }
+IPM_D FF ff_mul(FF a, FF b) {
+  const float p = __fmul_rn(a.h, b.h);
+  const float e = fmaf(a.h, b.h, -p);
+  return ff_fast_two_sum(p, __fadd_rn(e, fmaf(a.h, b.l, __fmul_rn(a.l, b.h))));
+}
+IPM_D double ff_to_double(FF a) { return (double)a.h + (double)a.l; }
+IPM_D FF ff_from_double(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+

@@ -208,6 +208,11 @@ __global__ void k_prep(GridDesc g, Stencil<double> st, IpmProblem pb, IpmBounds 
   if (write32) {
     dg.thy32[c] = (float)thy;
     dg.mh32[c] = (float)mh;
+    dg.thw32[c] = (float)thw;
+    dg.thv32[c] = (float)thv;
+    const FF t = ff_from_double(thy);
+    dg.thyff[c] = t.h;
+    dg.thyff[F + c] = t.l;
   }
   double My = st.mass(s.y, c);
   double Mu = st.mass_f(LdDiff<double>{s.w, s.v}, c);
@@ -375,8 +380,11 @@ __global__ void k_residuals(GridDesc g, Stencil<double> st, IpmProblem pb, IpmBo
 // [ 0          alpha M + Th_w    -alpha M        -M  ] [dw]
 // [ 0          -alpha M          alpha M + Th_v   M  ] [dv]
 // [ L          -M                M                0  ] [dp]
+// FP64 output, or (out_ff != null) float-float output: high parts of the four fields,
+// then their low parts (a float-float Krylov vector)
 __global__ void k_newton_apply(GridDesc g, Stencil<double> st, IpmProblem pb, IpmDiag dg,
-                               const double* __restrict__ x, double* __restrict__ out) {
+                               const double* __restrict__ x, double* __restrict__ out,
+                               float* __restrict__ out_ff) {
   int i, j, k;
   long long c;
   if (!interior_node(g, i, j, k, c)) return;
@@ -391,10 +399,19 @@ __global__ void k_newton_apply(GridDesc g, Stencil<double> st, IpmProblem pb, Ip
   double Ly = apply_L<double>(pb.L, st, Ld<double>{dy}, c, F);
   double LTp = apply_LT<double>(pb.L, st, Ld<double>{dp}, c, F);
   double a = pb.alpha;
-  out[c] = My + dg.thy[c] * dy[c] + LTp;
-  out[F + c] = a * Ms + dg.thw[c] * dw[c] - Mp;
-  out[2 * F + c] = -a * Ms + dg.thv[c] * dv[c] + Mp;
-  out[3 * F + c] = Ly - Ms;
+  const double r[4] = {My + dg.thy[c] * dy[c] + LTp, a * Ms + dg.thw[c] * dw[c] - Mp,
+                       -a * Ms + dg.thv[c] * dv[c] + Mp, Ly - Ms};
+  if (out_ff) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const FF v = ff_from_double(r[b]);
+      out_ff[b * F + c] = v.h;
+      out_ff[4 * F + b * F + c] = v.l;
+    }
+  } else {
+#pragma unroll
+    for (int b = 0; b < 4; ++b) out[b * F + c] = r[b];
+  }
 }
 
 // M_hat (and FP32 copies) from given diagonals, as in k_prep
@@ -409,6 +426,15 @@ __global__ void k_mhat(GridDesc g, double alpha, double dM, const double* __rest
   mh[c] = m;
   thy32[c] = (float)thy[c];
   mh32[c] = (float)m;
+}
+
+__global__ void k_to_float2(GridDesc g, const double* __restrict__ a, const double* __restrict__ b,
+                            float* __restrict__ a32, float* __restrict__ b32) {
+  int i, j, k;
+  long long c;
+  if (!interior_node(g, i, j, k, c)) return;
+  a32[c] = (float)a[c];
+  b32[c] = (float)b[c];
 }
 
 __global__ void k_reduce_cols(const double* __restrict__ part, long long nrows, int ncols,
@@ -498,12 +524,23 @@ void launch_newton_apply(const GridDesc& g, const IpmProblem& pb, const IpmDiag&
                          const double* x, double* y, cudaStream_t s) {
   count_launches(1);
   k_newton_apply<<<interior_grid(g), interior_block(), 0, s>>>(g, make_stencil<double>(g), pb, dg,
-                                                                x, y);
+                                                                x, y, nullptr);
+}
+void launch_newton_apply_ff(const GridDesc& g, const IpmProblem& pb, const IpmDiag& dg,
+                            const double* x, float* y, cudaStream_t s) {
+  count_launches(1);
+  k_newton_apply<<<interior_grid(g), interior_block(), 0, s>>>(g, make_stencil<double>(g), pb, dg,
+                                                                x, nullptr, y);
 }
 void launch_mhat(const GridDesc& g, double alpha, double dM, const double* thy, const double* thw,
                  const double* thv, double* mh, float* thy32, float* mh32, cudaStream_t s) {
   count_launches(1);
   k_mhat<<<interior_grid(g), interior_block(), 0, s>>>(g, alpha, dM, thy, thw, thv, mh, thy32, mh32);
+}
+void launch_to_float2(const GridDesc& g, const double* a, const double* b, float* a32, float* b32,
+                      cudaStream_t s) {
+  count_launches(1);
+  k_to_float2<<<interior_grid(g), interior_block(), 0, s>>>(g, a, b, a32, b32);
 }
 void launch_reduce_cols(const double* part, long long nrows, int ncols, double* out,
                         cudaStream_t s) {

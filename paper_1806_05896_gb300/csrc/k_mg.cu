@@ -161,53 +161,23 @@ __global__ void k_mg_outer(GridDesc g, Stencil<double> st, OpL L, const double* 
 
 // ---------------------------------------------------------------------------
 // Outer residual of the mixed multigrid solve in float-float arithmetic (2D Poisson).
-// A value is the unevaluated sum h + l of two floats (double-single). Error-free
-// transformations: TwoSum (Knuth), FastTwoSum (Dekker, |a| >= |b|), and the exact
-// product error of a fused multiply-add. Additions use the cheap form (one TwoSum plus
-// the low parts), whose error is about 2^-46 (|a| + |b|): the residual's absolute error
-// is then ~1e-13 |x|, far below what the FP32 cycles resolve, at FP32 instruction rates
-// (this GPU's FP64 rate is 1/64 of its FP32 rate). The _rn intrinsics keep the compiler
-// from contracting the transformations into fused multiply-adds.
+// Float-float arithmetic (FF, common.cuh): the residual's absolute error is ~1e-13 |x|,
+// far below what the FP32 cycles resolve, at FP32 instruction rates.
 // ---------------------------------------------------------------------------
-struct FF {
-  float h, l;
-};
-IPM_D FF ff_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, e};
-}
-IPM_D FF ff_fast_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-IPM_D FF ff_add(FF a, FF b) {
-  FF s = ff_two_sum(a.h, b.h);
-  return ff_fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
-}
-IPM_D FF ff_neg(FF a) { return {-a.h, -a.l}; }
-IPM_D FF ff_mul(FF a, FF b) {
-  const float p = __fmul_rn(a.h, b.h);
-  const float e = fmaf(a.h, b.h, -p);
-  return ff_fast_two_sum(p, __fadd_rn(e, fmaf(a.h, b.l, __fmul_rn(a.l, b.h))));
-}
-IPM_D FF ff_from_double(double x) {
-  const float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - (double)h)};
-}
-
 // x' = x + e (x = 0 when `first`), and either out64 = x' (last cycle) or
 // x' -> (xh_out, xl_out) and r32 = b - (L + diag m) x' rounded to FP32, evaluated as
 // (3b - (8 x'_c - sum of the 8 neighbours) - 3m x'_c) / 3. `first` also stores 3b
 // (from b64) as float-float for the later cycles; m3 = 3m as float-float.
+// The right-hand side comes as FP64 (b64) or as float-float planes (bff: high parts, then
+// low parts, g.field apart); the last cycle's x' goes to out64 or to float-float planes.
 __global__ void k_mg_outer_ff(GridDesc g, const float* __restrict__ xh_in,
                               const float* __restrict__ xl_in, const float* __restrict__ e,
-                              const double* __restrict__ b64, float* __restrict__ b3h,
-                              float* __restrict__ b3l, const float* __restrict__ m3h,
-                              const float* __restrict__ m3l, float* __restrict__ xh_out,
-                              float* __restrict__ xl_out, float* __restrict__ r32,
-                              double* __restrict__ out64, int first) {
+                              const double* __restrict__ b64, const float* __restrict__ bff,
+                              float* __restrict__ b3h, float* __restrict__ b3l,
+                              const float* __restrict__ m3h, const float* __restrict__ m3l,
+                              float* __restrict__ xh_out, float* __restrict__ xl_out,
+                              float* __restrict__ r32, double* __restrict__ out64,
+                              float* __restrict__ outff, int first) {
   int i, j, k;
   long long c;
   if (!interior_node(g, i, j, k, c)) return;
@@ -221,11 +191,16 @@ __global__ void k_mg_outer_ff(GridDesc g, const float* __restrict__ xh_in,
     out64[c] = (double)xc.h + (double)xc.l;
     return;
   }
+  if (outff) {
+    outff[c] = xc.h;
+    outff[g.field + c] = xc.l;
+    return;
+  }
   xh_out[c] = xc.h;
   xl_out[c] = xc.l;
   FF b3;
   if (first) {
-    b3 = ff_from_double(3.0 * b64[c]);
+    b3 = bff ? ff_mul(FF{bff[c], bff[g.field + c]}, FF{3.f, 0.f}) : ff_from_double(3.0 * b64[c]);
     b3h[c] = b3.h;
     b3l[c] = b3.l;
   } else {
@@ -268,13 +243,13 @@ void launch_mg_outer(const GridDesc& g, OpL L, const double* xprev, const float*
 }
 
 void launch_mg_outer_ff(const GridDesc& g, const float* xh_in, const float* xl_in, const float* e,
-                        const double* b64, float* b3h, float* b3l, const float* m3h,
-                        const float* m3l, float* xh_out, float* xl_out, float* r32, double* out64,
-                        int first, cudaStream_t s) {
+                        const double* b64, const float* bff, float* b3h, float* b3l,
+                        const float* m3h, const float* m3l, float* xh_out, float* xl_out,
+                        float* r32, double* out64, float* outff, int first, cudaStream_t s) {
   count_launches(1);
-  k_mg_outer_ff<<<interior_grid(g), interior_block(), 0, s>>>(g, xh_in, xl_in, e, b64, b3h, b3l,
-                                                              m3h, m3l, xh_out, xl_out, r32,
-                                                              out64, first);
+  k_mg_outer_ff<<<interior_grid(g), interior_block(), 0, s>>>(g, xh_in, xl_in, e, b64, bff, b3h,
+                                                              b3l, m3h, m3l, xh_out, xl_out, r32,
+                                                              out64, outff, first);
 }
 
 void launch_split3_ff(const GridDesc& g, const double* m, float* hi, float* lo, cudaStream_t s) {

@@ -751,13 +751,14 @@ __global__ void __launch_bounds__(512) k_cheb2_block(GridDesc g, ChebSteps cs, c
 // owner of a node keeps its b, Theta_y, 1 / (D_M + Theta_y) and previous iterate in
 // registers, the current iterate is exchanged through shared memory. Nodes outside the
 // domain carry a zero inverse diagonal and stay zero.
-template <int TX, int TY, int NS, int NW>
+template <int TX, int TY, int NS, int NW, typename Ti>
 __global__ void __launch_bounds__(NW * 32) k_cheb2_rb(GridDesc g, ChebSteps cs,
-                                                      const double* __restrict__ b,
+                                                      const Ti* __restrict__ b,
                                                       const float* __restrict__ thy,
                                                       const float* xc_in, const float* xp_in,
                                                       float* xc_out, float* xp_out,
-                                                      double* final_out, int first) {
+                                                      double* final_out, float* final32,
+                                                      int first) {
   constexpr int H = NS;
   using S = RBShape<TX, TY, H, NW>;
   constexpr int SX = S::SX, SY = S::SY, CX = S::CX, K = S::K;
@@ -854,6 +855,7 @@ __global__ void __launch_bounds__(NW * 32) k_cheb2_rb(GridDesc g, ChebSteps cs,
             const long long i = (long long)gy * p + gx;
             if (final_out) {
               final_out[i] = (double)v;
+              if (final32) final32[i] = v;
             } else {
               xc_out[i] = v;
               xp_out[i] = xc;
@@ -877,27 +879,30 @@ __global__ void __launch_bounds__(NW * 32) k_cheb2_rb(GridDesc g, ChebSteps cs,
   }
 }
 
-template <int TX, int TY, int NS, int NW>
-void cheb2_rb(const GridDesc& g, const ChebSteps& cs, const double* b, const float* thy,
+template <int TX, int TY, int NS, int NW, typename Ti>
+void cheb2_rb(const GridDesc& g, const ChebSteps& cs, const Ti* b, const float* thy,
               const float* xc_in, const float* xp_in, float* xc_out, float* xp_out,
-              double* final_out, int first, cudaStream_t s) {
+              double* final_out, float* final32, int first, cudaStream_t s) {
   static size_t set_to = 0;
   const size_t sm = RBShape<TX, TY, NS, NW>::smem;
-  ensure_smem_attr((const void*)k_cheb2_rb<TX, TY, NS, NW>, sm, set_to);
+  ensure_smem_attr((const void*)k_cheb2_rb<TX, TY, NS, NW, Ti>, sm, set_to);
   dim3 grid((g.n - 2 + TX - 1) / TX, (g.n - 2 + TY - 1) / TY);
   count_launches(1);
-  k_cheb2_rb<TX, TY, NS, NW><<<grid, NW * 32, sm, s>>>(g, cs, b, thy, xc_in, xp_in, xc_out,
-                                                        xp_out, final_out, first);
+  k_cheb2_rb<TX, TY, NS, NW, Ti><<<grid, NW * 32, sm, s>>>(g, cs, b, thy, xc_in, xp_in, xc_out,
+                                                            xp_out, final_out, final32, first);
 }
 
-// FP32 iterates: register-blocked kernels for blocks of 4 or 5 steps; true when launched
-template <int NS>
-bool cheb2_rb_dispatch(const GridDesc& g, const ChebSteps& cs, const double* b, const float* thy,
+// FP32 iterates: register-blocked kernels for blocks of 4 or 5 steps
+template <int NS, typename Ti>
+void cheb2_rb_dispatch(const GridDesc& g, const ChebSteps& cs, const Ti* b, const float* thy,
                        const float* xc_in, const float* xp_in, float* xc_out, float* xp_out,
-                       double* final_out, int first, cudaStream_t s) {
-  if (g.n > 513) cheb2_rb<56, 32, NS, 8>(g, cs, b, thy, xc_in, xp_in, xc_out, xp_out, final_out, first, s);
-  else cheb2_rb<24, 24, NS, 8>(g, cs, b, thy, xc_in, xp_in, xc_out, xp_out, final_out, first, s);
-  return true;
+                       double* final_out, float* final32, int first, cudaStream_t s) {
+  if (g.n > 513)
+    cheb2_rb<56, 32, NS, 8, Ti>(g, cs, b, thy, xc_in, xp_in, xc_out, xp_out, final_out, final32,
+                                first, s);
+  else
+    cheb2_rb<24, 24, NS, 8, Ti>(g, cs, b, thy, xc_in, xp_in, xc_out, xp_out, final_out, final32,
+                                first, s);
 }
 
 }  // namespace
@@ -909,11 +914,13 @@ void launch_cheb2_block(const GridDesc& g, const ChebSteps& cs, const Ti* b, con
   if constexpr (std::is_same<T, float>::value && std::is_same<Ti, double>::value &&
                 std::is_same<To, double>::value) {
     if (cs.ns == 5) {
-      cheb2_rb_dispatch<5>(g, cs, b, thy, xc_in, xp_in, xc_out, xp_out, final_out, first, s);
+      cheb2_rb_dispatch<5, double>(g, cs, b, thy, xc_in, xp_in, xc_out, xp_out, final_out,
+                                   nullptr, first, s);
       return;
     }
     if (cs.ns == 4) {
-      cheb2_rb_dispatch<4>(g, cs, b, thy, xc_in, xp_in, xc_out, xp_out, final_out, first, s);
+      cheb2_rb_dispatch<4, double>(g, cs, b, thy, xc_in, xp_in, xc_out, xp_out, final_out,
+                                   nullptr, first, s);
       return;
     }
   }
@@ -924,6 +931,22 @@ void launch_cheb2_block(const GridDesc& g, const ChebSteps& cs, const Ti* b, con
   count_launches(1);
   k_cheb2_block<T, Ti, To><<<grid, 512, sm, s>>>(g, cs, b, thy, xc_in, xp_in, xc_out, xp_out,
                                                  final_out, first);
+}
+
+// FP32 right-hand side (the high parts of a float-float vector) and an FP32 copy of the
+// final iterate; blocks of 4 or 5 steps (false otherwise: nothing launched)
+bool launch_cheb2_rb_f32(const GridDesc& g, const ChebSteps& cs, const float* b, const float* thy,
+                         const float* xc_in, const float* xp_in, float* xc_out, float* xp_out,
+                         double* final_out, float* final32, int first, cudaStream_t s) {
+  if (cs.ns == 5)
+    cheb2_rb_dispatch<5, float>(g, cs, b, thy, xc_in, xp_in, xc_out, xp_out, final_out, final32,
+                                first, s);
+  else if (cs.ns == 4)
+    cheb2_rb_dispatch<4, float>(g, cs, b, thy, xc_in, xp_in, xc_out, xp_out, final_out, final32,
+                                first, s);
+  else
+    return false;
+  return true;
 }
 
 #define IPM_CHEB2_INST(T, Ti, To)                                                              \

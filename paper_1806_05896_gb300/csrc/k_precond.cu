@@ -43,18 +43,20 @@ __global__ void k_cheb_step(GridDesc g, Stencil<T> st, const T* __restrict__ xc,
   out[c] = (To)xn;
 }
 
-__global__ void k_zblock(GridDesc g, double a, const double* __restrict__ rw,
-                         const double* __restrict__ rv, const double* __restrict__ thw,
-                         const double* __restrict__ thv, double* __restrict__ zw,
+// T: arithmetic (double, or float on the mixed path with FP32 copies of Theta)
+template <typename T>
+__global__ void k_zblock(GridDesc g, T a, const double* __restrict__ rw,
+                         const double* __restrict__ rv, const T* __restrict__ thw,
+                         const T* __restrict__ thv, double* __restrict__ zw,
                          double* __restrict__ zv) {
   int i, j, k;
   long long c;
   if (!interior_node(g, i, j, k, c)) return;
-  double tw = thw[c], tv = thv[c];
-  double det = a * (tw + tv) + tw * tv;  // (a + tw)(a + tv) - a^2
-  double r1 = rw[c], r2 = rv[c];
-  zw[c] = ((a + tv) * r1 + a * r2) / det;
-  zv[c] = (a * r1 + (a + tw) * r2) / det;
+  T tw = thw[c], tv = thv[c];
+  T det = a * (tw + tv) + tw * tv;  // (a + tw)(a + tv) - a^2
+  T r1 = (T)rw[c], r2 = (T)rv[c];
+  zw[c] = (double)(((a + tv) * r1 + a * r2) / det);
+  zv[c] = (double)((a * r1 + (a + tw) * r2) / det);
 }
 
 template <typename T>
@@ -93,6 +95,79 @@ __global__ void k_mass_theta(GridDesc g, Stencil<T> st, const T* __restrict__ x,
   out[c] = st.mass(x, c) + thy[c] * x[c];
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-precision P_T pieces with float-float data (2D Poisson), at FP32 instruction
+// rates: the z-block from FP32 right-hand sides, the Schur coupling and the
+// (M + Theta_y) product in float-float arithmetic.
+// ---------------------------------------------------------------------------
+// Q1 mass action without the h^2/36 factor, float-float (rows [1 4 1] (x) [1 4 1])
+template <typename LD>
+IPM_D FF mass2_raw_ff(const LD& x, long long c, long long p) {
+  auto row = [&](long long q) {
+    const FF a = x(q - 1), b = x(q), d = x(q + 1);
+    return ff_add(ff_add(a, FF{4.f * b.h, 4.f * b.l}), d);
+  };
+  const FF r1 = row(c);
+  return ff_add(ff_add(row(c - p), FF{4.f * r1.h, 4.f * r1.l}), row(c + p));
+}
+
+// z_w, z_v from FP32 right-hand sides (FP64 results and FP32 copies)
+__global__ void k_zblock32f(GridDesc g, float a, const float* __restrict__ rw,
+                            const float* __restrict__ rv, const float* __restrict__ thw,
+                            const float* __restrict__ thv, double* __restrict__ zw,
+                            double* __restrict__ zv, float* __restrict__ zw32,
+                            float* __restrict__ zv32) {
+  int i, j, k;
+  long long c;
+  if (!interior_node(g, i, j, k, c)) return;
+  const float tw = thw[c], tv = thv[c];
+  const float det = a * (tw + tv) + tw * tv;
+  const float r1 = rw[c], r2 = rv[c];
+  const float w = ((a + tv) * r1 + a * r2) / det;
+  const float v = (a * r1 + (a + tw) * r2) / det;
+  zw[c] = (double)w;
+  zv[c] = (double)v;
+  zw32[c] = w;
+  zv32[c] = v;
+}
+
+// t = L z_y - M (z_w - z_v) - r_p (z_* FP32, r_p and t float-float planes)
+__global__ void k_coupling_ff(GridDesc g, FF mscale, FF third, const float* __restrict__ zy,
+                              const float* __restrict__ zw, const float* __restrict__ zv,
+                              const float* __restrict__ rph, const float* __restrict__ rpl,
+                              float* __restrict__ th, float* __restrict__ tl) {
+  int i, j, k;
+  long long c;
+  if (!interior_node(g, i, j, k, c)) return;
+  const long long p = g.pitch;
+  // L z_y = (8 z_c - sum of the 8 neighbours) / 3
+  FF S = FF{zy[c - p - 1], 0.f};
+  const long long nb[7] = {c - p, c - p + 1, c - 1, c + 1, c + p - 1, c + p, c + p + 1};
+#pragma unroll
+  for (int q = 0; q < 7; ++q) S = ff_add(S, FF{zy[nb[q]], 0.f});
+  const FF Ly = ff_mul(ff_add(FF{8.f * zy[c], 0.f}, ff_neg(S)), third);
+  auto dwv = [&](long long q) { return ff_two_sum(zw[q], -zv[q]); };
+  const FF Ms = ff_mul(mass2_raw_ff(dwv, c, p), mscale);
+  const FF t = ff_add(ff_add(Ly, ff_neg(Ms)), FF{-rph[c], -rpl[c]});
+  th[c] = t.h;
+  tl[c] = t.l;
+}
+
+// out = M s + Theta_y s (float-float planes; Theta_y as float-float planes)
+__global__ void k_mass_theta_ff(GridDesc g, FF mscale, const float* __restrict__ sh,
+                                const float* __restrict__ sl, const float* __restrict__ tyh,
+                                const float* __restrict__ tyl, float* __restrict__ oh,
+                                float* __restrict__ ol) {
+  int i, j, k;
+  long long c;
+  if (!interior_node(g, i, j, k, c)) return;
+  auto x = [&](long long q) { return FF{sh[q], sl[q]}; };
+  const FF m = ff_mul(mass2_raw_ff(x, c, g.pitch), mscale);
+  const FF r = ff_add(m, ff_mul(FF{tyh[c], tyl[c]}, x(c)));
+  oh[c] = r.h;
+  ol[c] = r.l;
+}
+
 template <typename Ti, typename To>
 __global__ void k_convert(long long n, const Ti* __restrict__ x, To* __restrict__ y) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
@@ -119,7 +194,36 @@ void launch_cheb_step(const GridDesc& g, const T* xc, const T* xp, const T* bT, 
 void launch_zblock(const GridDesc& g, double adM, const double* rw, const double* rv,
                    const double* thw, const double* thv, double* zw, double* zv, cudaStream_t s) {
   count_launches(1);
-  k_zblock<<<interior_grid(g), interior_block(), 0, s>>>(g, adM, rw, rv, thw, thv, zw, zv);
+  k_zblock<double><<<interior_grid(g), interior_block(), 0, s>>>(g, adM, rw, rv, thw, thv, zw, zv);
+}
+void launch_zblock32(const GridDesc& g, double adM, const double* rw, const double* rv,
+                     const float* thw, const float* thv, double* zw, double* zv, cudaStream_t s) {
+  count_launches(1);
+  k_zblock<float><<<interior_grid(g), interior_block(), 0, s>>>(g, (float)adM, rw, rv, thw, thv, zw,
+                                                               zv);
+}
+static FF ff_host(double x) {
+  const float h = (float)x;
+  return FF{h, (float)(x - (double)h)};
+}
+void launch_zblock32f(const GridDesc& g, double adM, const float* rw, const float* rv,
+                      const float* thw, const float* thv, double* zw, double* zv, float* zw32,
+                      float* zv32, cudaStream_t s) {
+  count_launches(1);
+  k_zblock32f<<<interior_grid(g), interior_block(), 0, s>>>(g, (float)adM, rw, rv, thw, thv, zw,
+                                                            zv, zw32, zv32);
+}
+void launch_coupling_ff(const GridDesc& g, const float* zy, const float* zw, const float* zv,
+                        const float* rph, const float* rpl, float* th, float* tl, cudaStream_t s) {
+  count_launches(1);
+  k_coupling_ff<<<interior_grid(g), interior_block(), 0, s>>>(
+      g, ff_host(g.h * g.h / 36.0), ff_host(1.0 / 3.0), zy, zw, zv, rph, rpl, th, tl);
+}
+void launch_mass_theta_ff(const GridDesc& g, const float* sh, const float* sl, const float* tyh,
+                          const float* tyl, float* oh, float* ol, cudaStream_t s) {
+  count_launches(1);
+  k_mass_theta_ff<<<interior_grid(g), interior_block(), 0, s>>>(g, ff_host(g.h * g.h / 36.0), sh,
+                                                                sl, tyh, tyl, oh, ol);
 }
 template <typename T>
 void launch_coupling(const GridDesc& g, OpL L, const double* zy, const double* zw, const double* zv,

@@ -155,3 +155,219 @@ void launch_lincomb3(double* y, double a, const double* x1, double b, const doub
   count_launches(1);
   k_lincomb3<<<vec_blocks(len), 256, 0, s>>>(y, a, x1, b, x2, c, x3, len);
 }
+
+// ---------------------------------------------------------------------------
+// Float-float Krylov vectors: a 4-field vector of `len` entries stored as its high parts
+// (len floats) followed by its low parts (len floats), in the memory of an FP64 vector.
+// Products and sums run in float-float arithmetic; block partial sums are written in
+// FP64 and reduced in block order as in the FP64 kernels (bitwise reproducible).
+// ---------------------------------------------------------------------------
+namespace {
+
+IPM_D FF ff_at(const float* v, long long len, long long e) { return {v[e], v[len + e]}; }
+
+IPM_D FF warp_sum_ff(FF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    FF u{__shfl_down_sync(0xffffffffu, v.h, o), __shfl_down_sync(0xffffffffu, v.l, o)};
+    v = ff_add(v, u);
+  }
+  return v;
+}
+
+// sum over the block, valid in thread 0 (blockDim.x a multiple of 32, <= 1024)
+IPM_D FF block_sum_ff(FF v, FF* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum_ff(v);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  FF r{0.f, 0.f};
+  if (w == 0) {
+    if (lane < nw) r = sh[lane];
+    r = warp_sum_ff(r);
+  }
+  __syncthreads();
+  return r;
+}
+
+// Dot products in float-float: each term's exact product error (fused multiply-add) and
+// the running sum's TwoSum error go to a separate compensation sum (the scheme of
+// Ogita, Rump and Oishi's Dot2, with float-float inputs).
+__global__ void k_multidot_ff(const float* __restrict__ V, long long stride, int nv,
+                              const float* __restrict__ w, long long len,
+                              double* __restrict__ part) {
+  __shared__ FF sh[32];
+  float sum[kMaxDots], cmp[kMaxDots];
+#pragma unroll
+  for (int q = 0; q < kMaxDots; ++q) sum[q] = cmp[q] = 0.f;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
+       e += (long long)gridDim.x * blockDim.x) {
+    const FF we = ff_at(w, len, e);
+#pragma unroll
+    for (int q = 0; q < kMaxDots; ++q)
+      if (q < nv) {
+        const FF a = ff_at(V + q * stride, len, e);
+        const float p = __fmul_rn(a.h, we.h);
+        const float pe = fmaf(a.h, we.h, -p);
+        const FF s = ff_two_sum(sum[q], p);
+        sum[q] = s.h;
+        cmp[q] = __fadd_rn(cmp[q], __fadd_rn(__fadd_rn(pe, s.l), fmaf(a.h, we.l, __fmul_rn(a.l, we.h))));
+      }
+  }
+  for (int q = 0; q < nv; ++q) {
+    const FF r = block_sum_ff(ff_fast_two_sum(sum[q], cmp[q]), sh);
+    if (threadIdx.x == 0) part[(long long)blockIdx.x * kMaxDots + q] = ff_to_double(r);
+  }
+}
+
+// FP32 dot products of the high parts (the first Gram-Schmidt pass: the second, in
+// float-float, removes what this one leaves)
+__global__ void k_multidot_hi(const float* __restrict__ V, long long stride, int nv,
+                              const float* __restrict__ w, long long len,
+                              double* __restrict__ part) {
+  __shared__ float sh[32];
+  float acc[kMaxDots];
+#pragma unroll
+  for (int q = 0; q < kMaxDots; ++q) acc[q] = 0.f;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
+       e += (long long)gridDim.x * blockDim.x) {
+    const float we = w[e];
+#pragma unroll
+    for (int q = 0; q < kMaxDots; ++q)
+      if (q < nv) acc[q] = fmaf(V[q * stride + e], we, acc[q]);
+  }
+  for (int q = 0; q < nv; ++q) {
+    const float r = block_sum(acc[q], sh);
+    if (threadIdx.x == 0) part[(long long)blockIdx.x * kMaxDots + q] = (double)r;
+  }
+}
+
+// Squared norm of a float-float vector with per-thread power-of-two scaling (the squares
+// of entries above ~1e19 would overflow FP32): each thread keeps its sum scaled by 2^-2e,
+// e the largest exponent it has seen, and rescales exactly when a larger one appears.
+// Thread sums go to FP64 and are added in the fixed block order.
+__global__ void k_norm2_ff(const float* __restrict__ w, long long len, double* __restrict__ part) {
+  __shared__ double sh[32];
+  int emax = -200;
+  FF acc{0.f, 0.f};
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
+       e += (long long)gridDim.x * blockDim.x) {
+    const FF x = ff_at(w, len, e);
+    if (x.h == 0.f) continue;
+    int ex;
+    frexpf(x.h, &ex);
+    if (ex > emax) {
+      if (emax > -200) {
+        const int d = 2 * (emax - ex);
+        acc = FF{ldexpf(acc.h, d), ldexpf(acc.l, d)};
+      }
+      emax = ex;
+    }
+    const FF xs{ldexpf(x.h, -emax), ldexpf(x.l, -emax)};
+    acc = ff_add(acc, ff_mul(xs, xs));
+  }
+  double t = emax > -200 ? ldexp(ff_to_double(acc), 2 * emax) : 0.0;
+  t = block_sum(t, sh);
+  if (threadIdx.x == 0) part[(long long)blockIdx.x * kMaxDots] = t;
+}
+
+// FP64 sums of the block partials (block order); also the float-float value of each sum
+// and, for `rsqrt`, of 1 / sqrt(sum) (a squared norm)
+__global__ void k_reduce_dots_ff(const double* __restrict__ part, int nblocks, int nv,
+                                 double* __restrict__ out, float* __restrict__ out_ff, int rsqrt) {
+  __shared__ double sh[32];
+  const int q = blockIdx.x;
+  double acc = 0.0;
+  for (int r = threadIdx.x; r < nblocks; r += blockDim.x) acc += part[(long long)r * kMaxDots + q];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    out[q] = acc;
+    const FF v = ff_from_double(rsqrt ? 1.0 / sqrt(acc) : acc);
+    out_ff[2 * q] = v.h;
+    out_ff[2 * q + 1] = v.l;
+  }
+}
+
+// w += sign * sum_q coef[q] V_q (coef as float-float pairs)
+__global__ void k_axpy_multi_ff(float* __restrict__ w, const float* __restrict__ V,
+                                long long stride, int nv, const float* __restrict__ coef,
+                                float sign, long long len) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
+       e += (long long)gridDim.x * blockDim.x) {
+    FF acc{0.f, 0.f};
+    for (int q = 0; q < nv; ++q)
+      acc = ff_add(acc, ff_mul(FF{coef[2 * q], coef[2 * q + 1]}, ff_at(V + q * stride, len, e)));
+    const FF r = ff_add(ff_at(w, len, e), FF{sign * acc.h, sign * acc.l});
+    w[e] = r.h;
+    w[len + e] = r.l;
+  }
+}
+
+// v *= f (f a float-float pair on the device)
+__global__ void k_scale_ff(float* __restrict__ v, const float* __restrict__ f, long long len) {
+  const FF s{f[0], f[1]};
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
+       e += (long long)gridDim.x * blockDim.x) {
+    const FF r = ff_mul(ff_at(v, len, e), s);
+    v[e] = r.h;
+    v[len + e] = r.l;
+  }
+}
+
+// out = a * x (FP64 in, float-float out) and back (FP64 out)
+__global__ void k_to_ff(float* __restrict__ out, const double* __restrict__ x, double a,
+                        long long len) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
+       e += (long long)gridDim.x * blockDim.x) {
+    const FF r = ff_from_double(a * x[e]);
+    out[e] = r.h;
+    out[len + e] = r.l;
+  }
+}
+__global__ void k_from_ff(double* __restrict__ out, const float* __restrict__ v, long long len) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = ff_to_double(ff_at(v, len, e));
+}
+
+}  // namespace
+
+// float-float dots run on 4 x kRedBlocks blocks (latency of the compensated sums), the
+// FP32 ones on kRedBlocks; `hi` selects the FP32 dots of the high parts
+void launch_multidot_ff(const float* V, long long stride, int nv, const float* w, long long len,
+                        double* part, double* out, float* out_ff, int hi, cudaStream_t s) {
+  const int nb = hi ? kRedBlocks : 4 * kRedBlocks;
+  for (int q0 = 0; q0 < nv; q0 += kMaxDots) {
+    int m = nv - q0 < kMaxDots ? nv - q0 : kMaxDots;
+    count_launches(1);
+    if (hi) k_multidot_hi<<<nb, kRedThreads, 0, s>>>(V + q0 * stride, stride, m, w, len, part);
+    else k_multidot_ff<<<nb, kRedThreads, 0, s>>>(V + q0 * stride, stride, m, w, len, part);
+    count_launches(1);
+    k_reduce_dots_ff<<<m, 256, 0, s>>>(part, nb, m, out + q0, out_ff + 2 * q0, 0);
+  }
+}
+void launch_norm2_ff(const float* w, long long len, double* part, double* out, float* out_ff,
+                     cudaStream_t s) {
+  count_launches(1);
+  k_norm2_ff<<<kRedBlocks, kRedThreads, 0, s>>>(w, len, part);
+  count_launches(1);
+  k_reduce_dots_ff<<<1, 256, 0, s>>>(part, kRedBlocks, 1, out, out_ff, 1);
+}
+void launch_axpy_multi_ff(float* w, const float* V, long long stride, int nv, const float* coef,
+                          double sign, long long len, cudaStream_t s) {
+  count_launches(1);
+  k_axpy_multi_ff<<<vec_blocks(len), 256, 0, s>>>(w, V, stride, nv, coef, (float)sign, len);
+}
+void launch_scale_ff(float* v, const float* f, long long len, cudaStream_t s) {
+  count_launches(1);
+  k_scale_ff<<<vec_blocks(len), 256, 0, s>>>(v, f, len);
+}
+void launch_to_ff(float* out, const double* x, double a, long long len, cudaStream_t s) {
+  count_launches(1);
+  k_to_ff<<<vec_blocks(len), 256, 0, s>>>(out, x, a, len);
+}
+void launch_from_ff(double* out, const float* v, long long len, cudaStream_t s) {
+  count_launches(1);
+  k_from_ff<<<vec_blocks(len), 256, 0, s>>>(out, v, len);
+}

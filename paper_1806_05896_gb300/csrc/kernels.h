@@ -23,7 +23,8 @@ struct IpmBounds {  // +-inf marks an absent bound; the lower bounds of w and v 
 };
 struct IpmDiag {  // barrier diagonals and the Schur-approximation diagonal M_hat
   double *thy, *thw, *thv, *mh;
-  float *thy32, *mh32;
+  float *thy32, *mh32, *thw32, *thv32;
+  float* thyff;  // Theta_y as float-float planes (high parts, then low parts)
 };
 // Elliptic operator L: Poisson stiffness (stencil == nullptr) or a stored
 // 9-point stencil per node (convection-diffusion), coef[o * field + node] =
@@ -64,6 +65,9 @@ void launch_residuals(const GridDesc& g, const IpmProblem& pb, const IpmBounds& 
                       double mu, double* part, double* out, cudaStream_t s);
 void launch_newton_apply(const GridDesc& g, const IpmProblem& pb, const IpmDiag& dg,
                          const double* x, double* y, cudaStream_t s);
+// same operator, output as a float-float Krylov vector (high parts, then low parts)
+void launch_newton_apply_ff(const GridDesc& g, const IpmProblem& pb, const IpmDiag& dg,
+                            const double* x, float* y, cudaStream_t s);
 void launch_reduce_cols(const double* part, long long nrows, int ncols, double* out,
                         cudaStream_t s);
 long long interior_blocks(const GridDesc& g);
@@ -79,6 +83,17 @@ void launch_cheb_step(const GridDesc& g, const T* xc, const T* xp, const T* bT, 
                       double dM, double omega, double inv_theta, To* out, cudaStream_t s);
 void launch_zblock(const GridDesc& g, double adM, const double* rw, const double* rv,
                    const double* thw, const double* thv, double* zw, double* zv, cudaStream_t s);
+void launch_zblock32(const GridDesc& g, double adM, const double* rw, const double* rv,
+                     const float* thw, const float* thv, double* zw, double* zv, cudaStream_t s);
+// float-float P_T pieces (2D Poisson): z-block from FP32 right-hand sides (FP64 results and
+// FP32 copies), coupling t = L z_y - M(z_w - z_v) - r_p and (M + Theta_y) s as planes
+void launch_zblock32f(const GridDesc& g, double adM, const float* rw, const float* rv,
+                      const float* thw, const float* thv, double* zw, double* zv, float* zw32,
+                      float* zv32, cudaStream_t s);
+void launch_coupling_ff(const GridDesc& g, const float* zy, const float* zw, const float* zv,
+                        const float* rph, const float* rpl, float* th, float* tl, cudaStream_t s);
+void launch_mass_theta_ff(const GridDesc& g, const float* sh, const float* sl, const float* tyh,
+                          const float* tyl, float* oh, float* ol, cudaStream_t s);
 template <typename T>
 void launch_coupling(const GridDesc& g, OpL L, const double* zy, const double* zw, const double* zv,
                      const double* rp, int triangular, T* t, cudaStream_t s);
@@ -112,9 +127,9 @@ void launch_mg_outer(const GridDesc& g, OpL L, const double* xprev, const float*
                      cudaStream_t s);
 // float-float form of the outer step for the 2D Poisson operator (FP32 instruction rates)
 void launch_mg_outer_ff(const GridDesc& g, const float* xh_in, const float* xl_in, const float* e,
-                        const double* b64, float* b3h, float* b3l, const float* m3h,
-                        const float* m3l, float* xh_out, float* xl_out, float* r32, double* out64,
-                        int first, cudaStream_t s);
+                        const double* b64, const float* bff, float* b3h, float* b3l,
+                        const float* m3h, const float* m3l, float* xh_out, float* xl_out,
+                        float* r32, double* out64, float* outff, int first, cudaStream_t s);
 void launch_split3_ff(const GridDesc& g, const double* m, float* hi, float* lo, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
@@ -151,6 +166,9 @@ struct ChebSteps {
   double dM;      // diag(M)
   double mscale;  // h^2 / 36
 };
+bool launch_cheb2_rb_f32(const GridDesc& g, const ChebSteps& cs, const float* b, const float* thy,
+                         const float* xc_in, const float* xp_in, float* xc_out, float* xp_out,
+                         double* final_out, float* final32, int first, cudaStream_t s);
 template <typename T, typename Ti, typename To>
 void launch_cheb2_block(const GridDesc& g, const ChebSteps& cs, const Ti* b, const T* thy,
                         const T* xc_in, const T* xp_in, T* xc_out, T* xp_out, To* final_out,
@@ -167,6 +185,18 @@ void launch_to_float(long long n, const double* x, float* y, cudaStream_t s);
 // ----------------------------------------------------------------------------
 // k_vec.cu (Krylov vector kernels over whole field blocks, deterministic)
 // ----------------------------------------------------------------------------
+// float-float Krylov vectors (high parts, then low parts; `stride` and `len` in entries)
+// (hi = 1: FP32 dots of the high parts only; part needs 4 x kRedBlocks x 8 entries)
+void launch_multidot_ff(const float* V, long long stride, int nv, const float* w, long long len,
+                        double* part, double* out, float* out_ff, int hi, cudaStream_t s);
+// ||w||^2 in FP64 (overflow-safe) and 1/||w|| as a float-float pair
+void launch_norm2_ff(const float* w, long long len, double* part, double* out, float* out_ff,
+                     cudaStream_t s);
+void launch_axpy_multi_ff(float* w, const float* V, long long stride, int nv, const float* coef,
+                          double sign, long long len, cudaStream_t s);
+void launch_scale_ff(float* v, const float* f, long long len, cudaStream_t s);
+void launch_to_ff(float* out, const double* x, double a, long long len, cudaStream_t s);
+void launch_from_ff(double* out, const float* v, long long len, cudaStream_t s);
 void launch_multidot(const double* V, long long stride, int nv, const double* w, long long len,
                      double* part, double* out, cudaStream_t s);
 void launch_axpy_multi(double* w, const double* V, long long stride, int nv, const double* coef,
@@ -184,3 +214,6 @@ void launch_lincomb3(double* y, double a, const double* x1, double b, const doub
                      const double* x3, long long len, cudaStream_t s);
 void launch_mhat(const GridDesc& g, double alpha, double dM, const double* thy, const double* thw,
                  const double* thv, double* mh, float* thy32, float* mh32, cudaStream_t s);
+// FP32 copies of Theta_w, Theta_v (mixed-precision z-block)
+void launch_to_float2(const GridDesc& g, const double* a, const double* b, float* a32, float* b32,
+                      cudaStream_t s);

@@ -64,6 +64,13 @@ struct ipm_solver {
   double *rhs = nullptr, *dx = nullptr, *ktmp = nullptr;
   double *V = nullptr, *Z = nullptr;
   int vcap = 0;
+  // float-float Arnoldi basis (mixed precision): V_j holds high parts then low parts;
+  // kff holds the Gram-Schmidt coefficients and 1/||w|| as float-float pairs
+  bool krylov_ff = false;
+  float* kff = nullptr;
+  // layout of the basis entries the kernels never write (boundary and padding nodes, which
+  // must read as zero): -1 all zero, 0 FP64, 1 float-float
+  int vlayout = -1;
   double* mr[14] = {};
   double* cheb64[4] = {};
   float* cheb32[4] = {};
@@ -73,6 +80,8 @@ struct ipm_solver {
   float *mgb3 = nullptr, *mgm3 = nullptr;    // float-float 3b and 3m (high part, then low part)
   float* mgxf[2] = {};                       // float-float iterates (own buffers: the FP64 ones
                                              // keep zero boundaries in their own layout)
+  float* zf32 = nullptr;                     // FP32 copies of z_y, z_w, z_v (float-float P_T)
+  float* pff[3] = {};                        // float-float planes: t, S^{-1}-stage iterate, rhs
   bool ff_outer = true;
   // stored operator per multigrid level (convection-diffusion); empty for Poisson
   std::vector<OpL> lvop;
@@ -311,6 +320,11 @@ struct ipm_solver {
     dg.mh = alloc<double>(f);
     dg.thy32 = alloc<float>(f);
     dg.mh32 = alloc<float>(f);
+    dg.thw32 = alloc<float>(f);
+    dg.thv32 = alloc<float>(f);
+    dg.thyff = alloc<float>(2 * f);
+    zf32 = alloc<float>(3 * f);
+    for (int q = 0; q < 3; ++q) pff[q] = alloc<float>(2 * f);
     rhs = alloc<double>(4 * f);
     dx = alloc<double>(4 * f);
     ktmp = alloc<double>(4 * f);
@@ -331,6 +345,7 @@ struct ipm_solver {
     dout = alloc<double>(64);
     sc = alloc<double>(16);
     kdev = alloc<double>(4 * (kMaxRestart + 2));
+    kff = alloc<float>(2 * 4 * (kMaxRestart + 2));
     dense = alloc<double>(nn());
     set_bounds(bd);
   }
@@ -546,25 +561,36 @@ struct ipm_solver {
     if (use_ff_outer()) launch_split3_ff(g, dg.mh, mgm3, mgm3 + F(), stream);
   }
 
+  // float-float outer iterate (high part, then low part); right-hand side as FP64 (b64) or
+  // float-float planes (bff), result to FP64 (out) or float-float planes (outff)
+  void mg_solve_mixed_ff(const double* b64, const float* bff, double* out, float* outff, int tr,
+                         const ipm_options& o) {
+    MGLevel<float>& L0 = mg32.lv[0];
+    const int cycles = std::max(1, o.vcycles);
+    const long long f = F();
+    if (bff) CK(cudaMemcpyAsync(L0.b, bff, sizeof(float) * f, cudaMemcpyDeviceToDevice, stream));
+    else launch_convert<double, float>(g, b64, L0.b, stream);
+    for (int c = 0; c < cycles; ++c) {
+      if (fused_mg()) vcycle_fused(mg32, true, o);
+      else vcycle(mg32, 0, true, tr, o);
+      const float* e = L0.x[mg32.cur[0]];
+      const bool last = c == cycles - 1;
+      float* xin = mgxf[(c + 1) & 1];
+      float* xout = mgxf[c & 1];
+      launch_mg_outer_ff(g, xin, xin + f, e, b64, bff, mgb3, mgb3 + f, mgm3, mgm3 + f, xout,
+                         xout + f, last ? nullptr : L0.b, last ? out : nullptr,
+                         last ? outff : nullptr, c == 0 ? 1 : 0, stream);
+    }
+  }
+
   void mg_solve_mixed(const double* b64, double* out, int tr, const ipm_options& o) {
+    if (use_ff_outer()) {
+      mg_solve_mixed_ff(b64, nullptr, out, nullptr, tr, o);
+      return;
+    }
     MGLevel<float>& L0 = mg32.lv[0];
     const int cycles = std::max(1, o.vcycles);
     launch_convert<double, float>(g, b64, L0.b, stream);
-    if (use_ff_outer()) {
-      // iterate x as float-float (high part, then low part)
-      const long long f = F();
-      for (int c = 0; c < cycles; ++c) {
-        if (fused_mg()) vcycle_fused(mg32, true, o);
-        else vcycle(mg32, 0, true, tr, o);
-        const float* e = L0.x[mg32.cur[0]];
-        const bool last = c == cycles - 1;
-        float* xin = mgxf[(c + 1) & 1];
-        float* xout = mgxf[c & 1];
-        launch_mg_outer_ff(g, xin, xin + f, e, b64, mgb3, mgb3 + f, mgm3, mgm3 + f, xout, xout + f,
-                           last ? nullptr : L0.b, last ? out : nullptr, c == 0 ? 1 : 0, stream);
-      }
-      return;
-    }
     const double* xprev = nullptr;
     int xb = 0;
     for (int c = 0; c < cycles; ++c) {
@@ -660,7 +686,8 @@ struct ipm_solver {
   // z = P^{-1} r, P = P_T (tri) or P_D (Section 4.2)
   void precond(const double* r, double* z, int tri, const ipm_options& o) {
     long long f = F();
-    // kernel_flags bits 2 / 3 keep the Chebyshev / multigrid stage in FP64 on the mixed path
+    // kernel_flags bits 2 / 3 keep the Chebyshev and z-block / multigrid stage in FP64 on
+    // the mixed path
     bool mixed_cheb = o.precision == IPM_PREC_MIXED && !(o.kernel_flags & 4);
     bool mixed = o.precision == IPM_PREC_MIXED && !(o.kernel_flags & 8);
     int p1 = ph_begin(1);
@@ -668,8 +695,12 @@ struct ipm_solver {
     else cheb_apply<double, double>(r, dg.thy, z, o.cheb_steps, cheb64);
     ph_end(p1);
     int p2 = ph_begin(2);
-    launch_zblock(g, alpha * mass_diag(g), r + f, r + 2 * f, dg.thw, dg.thv, z + f, z + 2 * f,
-                  stream);
+    if (mixed_cheb)
+      launch_zblock32(g, alpha * mass_diag(g), r + f, r + 2 * f, dg.thw32, dg.thv32, z + f,
+                      z + 2 * f, stream);
+    else
+      launch_zblock(g, alpha * mass_diag(g), r + f, r + 2 * f, dg.thw, dg.thv, z + f, z + 2 * f,
+                    stream);
     if (mixed) launch_coupling<double>(g, opL(), z, z + f, z + 2 * f, r + 3 * f, tri, mgb64, stream);
     else launch_coupling<double>(g, opL(), z, z + f, z + 2 * f, r + 3 * f, tri, mg64.lv[0].b, stream);
     ph_end(p2);
@@ -702,6 +733,73 @@ struct ipm_solver {
     }
   }
 
+  // P_T^{-1} v for a float-float Krylov vector v (2D Poisson, mixed precision): the y- and
+  // z-blocks from the FP32 high parts, the coupling and the Schur stage in float-float, so
+  // that no FP64 arithmetic runs but the conversion of z to FP64 for the FGMRES basis Z.
+  bool precond_ff_ok(const ipm_options& o, int tri) const {
+    const int k = o.cheb_steps - 1;  // Chebyshev blocks of 5 steps, the last of 4 or 5
+    return tri && krylov_ff && use_ff_outer() && fused && fused_mg() && !(o.kernel_flags & 76) &&
+           k > 0 && (k % 5 == 0 || k % 5 == 4);
+  }
+
+  void cheb_apply_f32(const float* r32, double* z, float* z32, int steps) {
+    const double lmin = 0.25, lmax = 2.25;
+    double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sig = theta / delta;
+    std::vector<double> om(steps + 1, 0.0);
+    double rho = 1.0 / sig;
+    for (int k = 1; k < steps; ++k) {
+      double rho_new = 1.0 / (2.0 * sig - rho);
+      om[k] = 2.0 * sig * rho_new;
+      rho = rho_new;
+    }
+    ChebSteps cs;
+    cs.gamma = 1.0 / theta;
+    cs.dM = mass_diag(g);
+    cs.mscale = g.h * g.h / 36.0;
+    float* const* buf = cheb32;
+    int k = 1, pair = 0;
+    bool first = true;
+    while (true) {
+      int ns = std::min(5, steps - k);
+      cs.ns = ns;
+      for (int q = 0; q < ns; ++q) cs.omega[q] = om[k + q];
+      bool last = k + ns == steps;
+      if (!launch_cheb2_rb_f32(g, cs, r32, dg.thy32, buf[2 * pair], buf[2 * pair + 1],
+                               buf[2 * (1 - pair)], buf[2 * (1 - pair) + 1], last ? z : nullptr,
+                               last ? z32 : nullptr, first ? 1 : 0, stream))
+        throw IpmError{IPM_EINVAL, "Chebyshev block size without an FP32-input kernel"};
+      k += ns;
+      first = false;
+      pair = 1 - pair;
+      if (last) break;
+    }
+  }
+
+  void precond_ff(const float* v, double* z, const ipm_options& o) {
+    const long long f = F(), len = 4 * f;
+    const float* vh = v;
+    const float* vl = v + len;
+    int p1 = ph_begin(1);
+    cheb_apply_f32(vh, z, zf32, o.cheb_steps);
+    ph_end(p1);
+    int p2 = ph_begin(2);
+    launch_zblock32f(g, alpha * mass_diag(g), vh + f, vh + 2 * f, dg.thw32, dg.thv32, z + f,
+                     z + 2 * f, zf32 + f, zf32 + 2 * f, stream);
+    launch_coupling_ff(g, zf32, zf32 + f, zf32 + 2 * f, vh + 3 * f, vl + 3 * f, pff[0],
+                       pff[0] + f, stream);
+    ph_end(p2);
+    int p3 = ph_begin(3);
+    mg_solve_mixed_ff(nullptr, pff[0], nullptr, pff[1], 0, o);
+    ph_end(p3);
+    int p4 = ph_begin(4);
+    launch_mass_theta_ff(g, pff[1], pff[1] + f, dg.thyff, dg.thyff + f, pff[2], pff[2] + f,
+                         stream);
+    ph_end(p4);
+    int p5 = ph_begin(3);
+    mg_solve_mixed_ff(nullptr, pff[2], z + 3 * f, nullptr, 1, o);
+    ph_end(p5);
+  }
+
   void setup_precond(const ipm_options& o) {
     if (o.precision == IPM_PREC_MIXED && !(o.kernel_flags & 8)) mg_setup_mixed();
     else mg_setup(mg64, dg.mh);
@@ -725,6 +823,7 @@ struct ipm_solver {
         V = alloc<double>((long long)(o.restart + 1) * f4);
         Z = alloc<double>((long long)o.restart * f4);
         vcap = o.restart;
+        vlayout = -1;
       }
     } else if (!mr[0]) {
       for (int i = 0; i < 14; ++i) mr[i] = alloc<double>(f4);
@@ -735,7 +834,48 @@ struct ipm_solver {
   // normalise V_j by the squared norm left by step j-1, Z_j = P^{-1} V_j,
   // V_{j+1} = A Z_j, two classical Gram-Schmidt passes against V_0..V_j, the squared
   // norm of V_{j+1}, and a copy of the coefficients into the pinned host buffer.
+  // Float-float form of the step: V_j and w in float-float (Gram-Schmidt and norms at FP32
+  // instruction rates), Z_j and the operator in FP64; P^{-1} reads V_j converted to FP64.
+  void arnoldi_body_ff(const ipm_options& o, int j, long long stride, long long len, int tri) {
+    float* Vf = (float*)V;
+    const long long sf = 2 * stride;  // floats per basis vector
+    float* vj = Vf + (long long)j * sf;
+    double* zj = Z + (long long)j * stride;
+    float* w = Vf + (long long)(j + 1) * sf;
+    const int K = kMaxRestart + 2;
+    int p0 = ph_begin(5);
+    if (j > 0) launch_scale_ff(vj, kff + 2 * (2 * K), len, stream);
+    const bool pff_ok = precond_ff_ok(o, tri);
+    if (!pff_ok) launch_from_ff(ktmp, vj, len, stream);
+    ph_end(p0);
+    if (pff_ok) precond_ff(vj, zj, o);
+    else precond(ktmp, zj, tri, o);
+    int p1 = ph_begin(6);
+    launch_newton_apply_ff(g, problem(), dg, zj, w, stream);
+    ph_end(p1);
+    int p2 = ph_begin(7);
+    launch_multidot_ff(Vf, sf, j + 1, w, len, part, kdev, kff, 1, stream);
+    ph_end(p2);
+    int p3 = ph_begin(8);
+    launch_axpy_multi_ff(w, Vf, sf, j + 1, kff, -1.0, len, stream);
+    ph_end(p3);
+    int p4 = ph_begin(7);
+    launch_multidot_ff(Vf, sf, j + 1, w, len, part, kdev + K, kff + 2 * K, 0, stream);
+    ph_end(p4);
+    int p5 = ph_begin(8);
+    launch_axpy_multi_ff(w, Vf, sf, j + 1, kff + 2 * K, -1.0, len, stream);
+    ph_end(p5);
+    int p6 = ph_begin(5);
+    launch_norm2_ff(w, len, part, kdev + 2 * K, kff + 2 * (2 * K), stream);
+    ph_end(p6);
+    CK(cudaMemcpyAsync(hbuf, kdev, sizeof(double) * (2 * K + 1), cudaMemcpyDeviceToHost, stream));
+  }
+
   void arnoldi_body(const ipm_options& o, int j, long long stride, long long len, int tri) {
+    if (krylov_ff) {
+      arnoldi_body_ff(o, j, stride, len, tri);
+      return;
+    }
     double* vj = V + (long long)j * stride;
     double* zj = Z + (long long)j * stride;
     double* w = V + (long long)(j + 1) * stride;
@@ -767,6 +907,7 @@ struct ipm_solver {
 
   void arnoldi_step(const ipm_options& o, int j, long long stride, long long len, int tri) {
     long long key = ((long long)o.precision << 40) ^ ((long long)tri << 39) ^
+                    ((long long)(krylov_ff ? 1 : 0) << 38) ^
                     ((long long)o.cheb_steps << 30) ^ ((long long)o.vcycles << 24) ^
                     ((long long)o.smooth_pre << 16) ^ ((long long)o.smooth_post << 8) ^
                     ((long long)(fused ? 1 : 0) << 4) ^ ((long long)o.kernel_flags << 48) ^
@@ -828,6 +969,14 @@ struct ipm_solver {
     if (nb == 0.0) return;
     double tol = o.krylov_tol * nb;
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+    // mixed precision: float-float Arnoldi basis (kernel_flags bit 5 keeps it in FP64)
+    krylov_ff = o.precision == IPM_PREC_MIXED && !(o.kernel_flags & 32);
+    // the operator writes interior nodes only: when the basis changes layout, the other
+    // entries of the old one would read as nonzero in the new one
+    const int lay = krylov_ff ? 1 : 0;
+    if (vlayout != -1 && vlayout != lay)
+      CK(cudaMemsetAsync(V, 0, sizeof(double) * (size_t)(vcap + 1) * len, stream));
+    vlayout = lay;
     int total = 0;
     bool first = true;
     double res = nb;
@@ -840,7 +989,8 @@ struct ipm_solver {
         res = norm(ktmp, len);
         if (res <= tol || total >= o.max_krylov) break;
       }
-      launch_axpby(V, r0, 1.0 / res, 0.0, len, stream);
+      if (krylov_ff) launch_to_ff((float*)V, r0, 1.0 / res, len, stream);
+      else launch_axpby(V, r0, 1.0 / res, 0.0, len, stream);
       std::fill(gv.begin(), gv.end(), 0.0);
       gv[0] = res;
       int j = 0;
@@ -1320,6 +1470,8 @@ static void load_diags(ipm_solver* s, const double* ty, const double* tw, const 
   launch_pack(s->g, tv, s->dg.thv, 1, s->stream);
   launch_mhat(s->g, s->alpha, mass_diag(s->g), s->dg.thy, s->dg.thw, s->dg.thv, s->dg.mh,
               s->dg.thy32, s->dg.mh32, s->stream);
+  launch_to_float2(s->g, s->dg.thw, s->dg.thv, s->dg.thw32, s->dg.thv32, s->stream);
+  launch_to_ff(s->dg.thyff, s->dg.thy, 1.0, s->F(), s->stream);
 }
 
 int ipm_precond_apply_device(ipm_solver* s, const ipm_options* opt, int tri, const double* ty,
@@ -1334,7 +1486,15 @@ int ipm_precond_apply_device(ipm_solver* s, const ipm_options* opt, int tri, con
     load_diags(s, ty, tw, tv);
     s->setup_precond(o);
     for (int b = 0; b < 4; ++b) launch_pack(s->g, r + b * m, s->rhs + b * f, 1, s->stream);
-    s->precond(s->rhs, s->dx, tri, o);
+    // the mixed FGMRES path applies P_T to float-float Krylov vectors: take that path too
+    s->krylov_ff = o.precision == IPM_PREC_MIXED && !(o.kernel_flags & 32);
+    if (s->precond_ff_ok(o, tri)) {
+      float* v = (float*)s->ktmp;
+      launch_to_ff(v, s->rhs, 1.0, 4 * f, s->stream);
+      s->precond_ff(v, s->dx, o);
+    } else {
+      s->precond(s->rhs, s->dx, tri, o);
+    }
     for (int b = 0; b < 4; ++b) launch_unpack(s->g, s->dx + b * f, nullptr, z + b * m, s->stream);
     s->sync();
     return IPM_OK;

@@ -70,8 +70,8 @@ def test_mixed_vcycle_tile_kernels(n):
 @pytest.mark.parametrize("n", [129, 257, 513, 1025])
 def test_mixed_preconditioner_tile_kernels(n):
     """P_T^{-1} r in mixed precision (FP32 Chebyshev and V-cycle tile kernels): the y-block
-    is the oracle's 20-step Chebyshev to FP32 accuracy, the (w, v)-block equals the FP64
-    path's, and the fused kernels give the per-sweep kernels' result."""
+    is the oracle's 20-step Chebyshev to FP32 accuracy, the (w, v)-block the FP64 path's
+    to FP32 accuracy, and the fused kernels give the per-sweep kernels' result."""
     torch = torch_cuda()
     qp = Q.build(2, n, 1e-2, 1e-3, -2.0, 1.5)
     rng = np.random.default_rng(n + 1)
@@ -91,8 +91,8 @@ def test_mixed_preconditioner_tile_kernels(n):
     A = (qp.M + sp.diags(th[0])).tocsr()
     zy = blocks.chebyshev(A, qp.dM + th[0], r[:nI], 20, lo, hi)
     assert rel(zi[:nI], zy) < 1e-5
-    # the (w, v)-block is exact pointwise 2x2 algebra in FP64 on both paths
-    assert rel(zi[nI:3 * nI], z64[nI:3 * nI]) < 1e-12
+    # the (w, v)-block: pointwise 2x2 solves, in FP32 on the mixed path
+    assert rel(zi[nI:3 * nI], z64[nI:3 * nI]) < 1e-6
     for a, b in ((zi, zs), (zi, z64)):
         for k in range(4):
             blk = slice(k * nI, (k + 1) * nI)
@@ -119,7 +119,8 @@ def test_newton_apply_full_size(full):
 def test_newton_step_full_size_solves_oracle_system(full, prec):
     """The Krylov Newton direction at 1025^2 (FGMRES + P_T, the benchmarked solver) solves
     the oracle's Newton system: relative residual ||A dx - rhs|| / ||rhs|| with the
-    oracle's matrix and right-hand side at the oracle's starting iterate."""
+    oracle's matrix and right-hand side at the oracle's starting iterate. The mixed path's
+    float-float Arnoldi basis needs the same iterations as an FP64 basis."""
     torch = torch_cuda()
     wl, qp, s = full
     st = oipm.initial_state(qp)
@@ -134,6 +135,12 @@ def test_newton_step_full_size_solves_oracle_system(full, prec):
     res = np.linalg.norm(A @ got - rhs) / np.linalg.norm(rhs)
     assert rr < 1.5e-10 and res < 2e-10
     assert 0 < it < 100
+    if prec == ipm.PREC_MIXED:
+        # the float-float Arnoldi basis converges like an FP64 one (kernel_flags bit 5)
+        it64, rr64 = s.newton_step([dev(a) for a in iterate_arrays(qp, st)], mu, dx,
+                                   krylov=ipm.KRYLOV_GMRES_PT, precision=prec, krylov_tol=1e-10,
+                                   max_krylov=200, kernel_flags=32)
+        assert abs(it - it64) <= 1 and rr64 < 1.5e-10
 
 
 def test_full_size_solve_properties(full):
