@@ -193,7 +193,16 @@ IPM_D FF block_sum_ff(FF v, FF* sh) {
 
 // Dot products in float-float: each term's exact product error (fused multiply-add) and
 // the running sum's TwoSum error go to a separate compensation sum (the scheme of
-// Ogita, Rump and Oishi's Dot2, with float-float inputs).
+// Ogita, Rump and Oishi's Dot2, with float-float inputs). Four consecutive entries per
+// thread and step (16-byte loads; len is a multiple of 4 and every vector 16-byte aligned).
+IPM_D void dot2_step(float& sum, float& cmp, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  const float pe = fmaf(ah, bh, -p);
+  const FF s = ff_two_sum(sum, p);
+  sum = s.h;
+  cmp = __fadd_rn(cmp, __fadd_rn(__fadd_rn(pe, s.l), fmaf(ah, bl, __fmul_rn(al, bh))));
+}
+
 __global__ void k_multidot_ff(const float* __restrict__ V, long long stride, int nv,
                               const float* __restrict__ w, long long len,
                               double* __restrict__ part) {
@@ -201,18 +210,21 @@ __global__ void k_multidot_ff(const float* __restrict__ V, long long stride, int
   float sum[kMaxDots], cmp[kMaxDots];
 #pragma unroll
   for (int q = 0; q < kMaxDots; ++q) sum[q] = cmp[q] = 0.f;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
+  const long long len4 = len >> 2;
+  const float4* wh = reinterpret_cast<const float4*>(w);
+  const float4* wl = reinterpret_cast<const float4*>(w + len);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len4;
        e += (long long)gridDim.x * blockDim.x) {
-    const FF we = ff_at(w, len, e);
+    const float4 bh = wh[e], bl = wl[e];
 #pragma unroll
     for (int q = 0; q < kMaxDots; ++q)
       if (q < nv) {
-        const FF a = ff_at(V + q * stride, len, e);
-        const float p = __fmul_rn(a.h, we.h);
-        const float pe = fmaf(a.h, we.h, -p);
-        const FF s = ff_two_sum(sum[q], p);
-        sum[q] = s.h;
-        cmp[q] = __fadd_rn(cmp[q], __fadd_rn(__fadd_rn(pe, s.l), fmaf(a.h, we.l, __fmul_rn(a.l, we.h))));
+        const float4 ah = reinterpret_cast<const float4*>(V + q * stride)[e];
+        const float4 al = reinterpret_cast<const float4*>(V + q * stride + len)[e];
+        dot2_step(sum[q], cmp[q], ah.x, al.x, bh.x, bl.x);
+        dot2_step(sum[q], cmp[q], ah.y, al.y, bh.y, bl.y);
+        dot2_step(sum[q], cmp[q], ah.z, al.z, bh.z, bl.z);
+        dot2_step(sum[q], cmp[q], ah.w, al.w, bh.w, bl.w);
       }
   }
   for (int q = 0; q < nv; ++q) {
@@ -230,12 +242,20 @@ __global__ void k_multidot_hi(const float* __restrict__ V, long long stride, int
   float acc[kMaxDots];
 #pragma unroll
   for (int q = 0; q < kMaxDots; ++q) acc[q] = 0.f;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
+  const long long len4 = len >> 2;
+  const float4* w4 = reinterpret_cast<const float4*>(w);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len4;
        e += (long long)gridDim.x * blockDim.x) {
-    const float we = w[e];
+    const float4 b = w4[e];
 #pragma unroll
     for (int q = 0; q < kMaxDots; ++q)
-      if (q < nv) acc[q] = fmaf(V[q * stride + e], we, acc[q]);
+      if (q < nv) {
+        const float4 a = reinterpret_cast<const float4*>(V + q * stride)[e];
+        acc[q] = fmaf(a.x, b.x, acc[q]);
+        acc[q] = fmaf(a.y, b.y, acc[q]);
+        acc[q] = fmaf(a.z, b.z, acc[q]);
+        acc[q] = fmaf(a.w, b.w, acc[q]);
+      }
   }
   for (int q = 0; q < nv; ++q) {
     const float r = block_sum(acc[q], sh);
@@ -289,18 +309,33 @@ __global__ void k_reduce_dots_ff(const double* __restrict__ part, int nblocks, i
   }
 }
 
-// w += sign * sum_q coef[q] V_q (coef as float-float pairs)
+// w += sign * sum_q coef[q] V_q (coef as float-float pairs), four entries per step
 __global__ void k_axpy_multi_ff(float* __restrict__ w, const float* __restrict__ V,
                                 long long stride, int nv, const float* __restrict__ coef,
                                 float sign, long long len) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
+  const long long len4 = len >> 2;
+  float4* wh = reinterpret_cast<float4*>(w);
+  float4* wl = reinterpret_cast<float4*>(w + len);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len4;
        e += (long long)gridDim.x * blockDim.x) {
-    FF acc{0.f, 0.f};
-    for (int q = 0; q < nv; ++q)
-      acc = ff_add(acc, ff_mul(FF{coef[2 * q], coef[2 * q + 1]}, ff_at(V + q * stride, len, e)));
-    const FF r = ff_add(ff_at(w, len, e), FF{sign * acc.h, sign * acc.l});
-    w[e] = r.h;
-    w[len + e] = r.l;
+    FF acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    for (int q = 0; q < nv; ++q) {
+      const FF cq{coef[2 * q], coef[2 * q + 1]};
+      const float4 ah = reinterpret_cast<const float4*>(V + q * stride)[e];
+      const float4 al = reinterpret_cast<const float4*>(V + q * stride + len)[e];
+      acc[0] = ff_add(acc[0], ff_mul(cq, FF{ah.x, al.x}));
+      acc[1] = ff_add(acc[1], ff_mul(cq, FF{ah.y, al.y}));
+      acc[2] = ff_add(acc[2], ff_mul(cq, FF{ah.z, al.z}));
+      acc[3] = ff_add(acc[3], ff_mul(cq, FF{ah.w, al.w}));
+    }
+    float4 h = wh[e], l = wl[e];
+    FF r;
+    r = ff_add(FF{h.x, l.x}, FF{sign * acc[0].h, sign * acc[0].l}); h.x = r.h; l.x = r.l;
+    r = ff_add(FF{h.y, l.y}, FF{sign * acc[1].h, sign * acc[1].l}); h.y = r.h; l.y = r.l;
+    r = ff_add(FF{h.z, l.z}, FF{sign * acc[2].h, sign * acc[2].l}); h.z = r.h; l.z = r.l;
+    r = ff_add(FF{h.w, l.w}, FF{sign * acc[3].h, sign * acc[3].l}); h.w = r.h; l.w = r.l;
+    wh[e] = h;
+    wl[e] = l;
   }
 }
 
@@ -333,11 +368,11 @@ __global__ void k_from_ff(double* __restrict__ out, const float* __restrict__ v,
 
 }  // namespace
 
-// float-float dots run on 4 x kRedBlocks blocks (latency of the compensated sums), the
-// FP32 ones on kRedBlocks; `hi` selects the FP32 dots of the high parts
+// 4 x kRedBlocks blocks (memory-level parallelism); `hi` selects the FP32 dots of the
+// high parts
 void launch_multidot_ff(const float* V, long long stride, int nv, const float* w, long long len,
                         double* part, double* out, float* out_ff, int hi, cudaStream_t s) {
-  const int nb = hi ? kRedBlocks : 4 * kRedBlocks;
+  const int nb = 4 * kRedBlocks;
   for (int q0 = 0; q0 < nv; q0 += kMaxDots) {
     int m = nv - q0 < kMaxDots ? nv - q0 : kMaxDots;
     count_launches(1);
@@ -357,7 +392,7 @@ void launch_norm2_ff(const float* w, long long len, double* part, double* out, f
 void launch_axpy_multi_ff(float* w, const float* V, long long stride, int nv, const float* coef,
                           double sign, long long len, cudaStream_t s) {
   count_launches(1);
-  k_axpy_multi_ff<<<vec_blocks(len), 256, 0, s>>>(w, V, stride, nv, coef, (float)sign, len);
+  k_axpy_multi_ff<<<vec_blocks(len / 4), 256, 0, s>>>(w, V, stride, nv, coef, (float)sign, len);
 }
 void launch_scale_ff(float* v, const float* f, long long len, cudaStream_t s) {
   count_launches(1);
