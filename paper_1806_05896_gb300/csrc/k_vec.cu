@@ -266,26 +266,40 @@ __global__ void k_multidot_hi(const float* __restrict__ V, long long stride, int
 // Squared norm of a float-float vector with per-thread power-of-two scaling (the squares
 // of entries above ~1e19 would overflow FP32): each thread keeps its sum scaled by 2^-2e,
 // e the largest exponent it has seen, and rescales exactly when a larger one appears.
-// Thread sums go to FP64 and are added in the fixed block order.
+// Four consecutive entries per step; thread sums go to FP64 and are added in the fixed
+// block order.
+IPM_D void norm2_step(FF& acc, int& emax, float& scale, float xh, float xl) {
+  if (xh == 0.f) return;
+  int ex;
+  frexpf(xh, &ex);
+  ex = ex < -100 ? -100 : ex;  // keeps 2^-ex finite for subnormal entries
+  if (ex > emax) {
+    if (emax > -200) {
+      const int d = 2 * (emax - ex);
+      acc = FF{ldexpf(acc.h, d), ldexpf(acc.l, d)};
+    }
+    emax = ex;
+    scale = ldexpf(1.f, -ex);  // exact power of two in [2^-128, 2^100]
+  }
+  const FF xs{xh * scale, xl * scale};
+  acc = ff_add(acc, ff_mul(xs, xs));
+}
+
 __global__ void k_norm2_ff(const float* __restrict__ w, long long len, double* __restrict__ part) {
   __shared__ double sh[32];
   int emax = -200;
+  float scale = 1.f;
   FF acc{0.f, 0.f};
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
+  const long long len4 = len >> 2;
+  const float4* wh = reinterpret_cast<const float4*>(w);
+  const float4* wl = reinterpret_cast<const float4*>(w + len);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len4;
        e += (long long)gridDim.x * blockDim.x) {
-    const FF x = ff_at(w, len, e);
-    if (x.h == 0.f) continue;
-    int ex;
-    frexpf(x.h, &ex);
-    if (ex > emax) {
-      if (emax > -200) {
-        const int d = 2 * (emax - ex);
-        acc = FF{ldexpf(acc.h, d), ldexpf(acc.l, d)};
-      }
-      emax = ex;
-    }
-    const FF xs{ldexpf(x.h, -emax), ldexpf(x.l, -emax)};
-    acc = ff_add(acc, ff_mul(xs, xs));
+    const float4 h = wh[e], l = wl[e];
+    norm2_step(acc, emax, scale, h.x, l.x);
+    norm2_step(acc, emax, scale, h.y, l.y);
+    norm2_step(acc, emax, scale, h.z, l.z);
+    norm2_step(acc, emax, scale, h.w, l.w);
   }
   double t = emax > -200 ? ldexp(ff_to_double(acc), 2 * emax) : 0.0;
   t = block_sum(t, sh);
@@ -385,9 +399,9 @@ void launch_multidot_ff(const float* V, long long stride, int nv, const float* w
 void launch_norm2_ff(const float* w, long long len, double* part, double* out, float* out_ff,
                      cudaStream_t s) {
   count_launches(1);
-  k_norm2_ff<<<kRedBlocks, kRedThreads, 0, s>>>(w, len, part);
+  k_norm2_ff<<<4 * kRedBlocks, kRedThreads, 0, s>>>(w, len, part);
   count_launches(1);
-  k_reduce_dots_ff<<<1, 256, 0, s>>>(part, kRedBlocks, 1, out, out_ff, 1);
+  k_reduce_dots_ff<<<1, 256, 0, s>>>(part, 4 * kRedBlocks, 1, out, out_ff, 1);
 }
 void launch_axpy_multi_ff(float* w, const float* V, long long stride, int nv, const float* coef,
                           double sign, long long len, cudaStream_t s) {
