@@ -413,6 +413,46 @@ def serving(ipm, W, np, num):
                    "log-uniform alpha, beta, Gaussian-sum y_d, mixed precision, kkt_rel 1e-6"}
 
 
+def sweep_table(sizes):
+    """The (alpha, beta) sweep on several grids: iteration counts, solve times, sparsity."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_1806_05896_gb300 import ipm
+
+    torch.cuda.set_device(0)
+    rows = []
+    for n in sizes:
+        interior = np.zeros((n, n), bool)
+        interior[1:-1, 1:-1] = True
+        interior = interior.reshape(-1)
+        for c in range(9):
+            wl = W.workload_c2(n=n, cell=c)
+            s = ipm.Solver(2, n, wl.alpha, wl.beta, wl.ua, wl.ub, wl.ya, wl.yb)
+            s.set_data(wl.yd)
+            for prec, name in ((ipm.PREC_MIXED, "mixed"), (ipm.PREC_FP64, "fp64")):
+                o = ipm.default_options(precision=prec, krylov=ipm.KRYLOV_GMRES_PT,
+                                        stop=ipm.STOP_KKT, kkt_tol=1e-6, common_step=1,
+                                        max_ipm=60)
+                s.solve(o)  # first solve captures the CUDA graphs
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = s.solve(o)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                u = s.control().reshape(-1)[interior]
+                h = 1.0 / (n - 1)
+                rows.append({"n": n, "alpha": wl.alpha, "beta": wl.beta, "precision": name,
+                             "ipm_iters": r["ipm_iters"],
+                             "krylov_per_ipm": r["krylov_iters_total"] / max(r["ipm_iters"], 1),
+                             "ms": dt * 1e3, "kkt_rel": r["kkt_rel"],
+                             "sparsity_pct": 100.0 * float(np.mean(np.abs(u) < 1e-2)),
+                             "u_l1": h * h * float(np.abs(u).sum())})
+            s.close()
+    print(json.dumps({"sweep_table": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -425,7 +465,12 @@ def main():
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--cells", type=int, default=0, help="sweep cells per rank (0 = all nine)")
     ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--sweep-table", default="",
+                    help="comma-separated grid sizes: print the (alpha, beta) sweep table and exit")
     args = ap.parse_args()
+    if args.sweep_table:
+        sweep_table([int(v) for v in args.sweep_table.split(",")])
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
