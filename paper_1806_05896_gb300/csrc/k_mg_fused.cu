@@ -4,11 +4,14 @@
 // jinv = omega / (8/3 + m), residual, full-weighting restriction P^T, bilinear
 // prolongation P), but each launch does many sweeps on a shared-memory tile:
 //
-//  k_mg2_pre_restrict  nu sweeps on a 64x32 tile + halo (nu + 2), then the residual
-//                      and the restriction onto the coarse nodes the tile owns;
+//  k_mg2_pre_restrict  nu sweeps on a tile + halo (nu + 2), then the residual and
+//                      the restriction onto the coarse nodes the tile owns;
 //  k_mg2_prolong_post  x + P x_c on the tile + halo nu, then nu sweeps;
-//  k_mg2_coarse        one CTA runs the whole V-cycle on all levels at or below
-//                      65^2 (FP32) / 33^2 (FP64) in shared memory.
+//  k_mg2_coarse        one CTA runs the whole V-cycle on all coarse levels (the
+//                      caller picks them: up to 65^2 in FP32, 9^2 in FP64) in shared
+//                      memory.
+// The _rb forms of the first two (FP32, 5 sweeps) keep each thread's nodes in registers;
+// k_cheb2_block / k_cheb2_rb do the same for blocks of Chebyshev steps.
 //
 // A V-cycle on a 1025^2 grid thus takes 2 launches per level above the coarse
 // block plus one, instead of about 14 per level.

@@ -706,7 +706,8 @@ struct ipm_solver {
     ph_end(p2);
     if (mixed) {
       // S_hat^{-1} t = (L + M_hat)^{-T} (M + Theta_y) (L + M_hat)^{-1} t, FP32 cycles with
-      // FP64 outer residuals; s1 is kept in FP64 for the (M + Theta_y) product
+      // float-float (2D Poisson) or FP64 outer residuals; s1 is kept in FP64 for the
+      // (M + Theta_y) product
       double* s1 = mg64.lv[0].r;  // an FP64 field of the finest level, free during this solve
       int p3 = ph_begin(3);
       mg_solve_mixed(mgb64, s1, 0, o);
@@ -1523,7 +1524,8 @@ int ipm_vcycle_device(ipm_solver* s, const ipm_options* opt, int tr, const doubl
     s->apply_flags(o);
     launch_pack(s->g, m, s->dg.mh, 1, s->stream);
     if (o.precision == IPM_PREC_MIXED) {
-      // the preconditioner's mixed solve: FP32 cycles, FP64 outer residual and iterate
+      // the preconditioner's mixed solve: FP32 cycles, outer residual and iterate in
+      // float-float (2D Poisson) or FP64
       launch_convert<double, float>(s->g, s->dg.mh, s->dg.mh32, s->stream);
       s->mg_setup_mixed();
       launch_pack(s->g, b, s->mgb64, 1, s->stream);
