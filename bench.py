@@ -41,6 +41,28 @@ ROOF_SRC = ("paper_1806_05896_gb300/csrc/k_mg_fused.cu",
             "__global__ void __launch_bounds__(NW * 32) k_mg2_prolong_post_rb")
 
 
+def rank_cells(rank: int, world: int, limit: int = 0) -> list:
+    """Sweep cells solved by `rank` of `world` replicas: cells c with c % world == rank (one
+    cell per rank beyond nine ranks); at most `limit` of them when limit > 0."""
+    cells = [c for c in range(9) if c % world == rank] or [rank % 9]
+    return cells[:limit] if limit > 0 else cells
+
+
+def max_over_ranks(x: float, dist_mod=None, device="cpu") -> float:
+    """Largest value of x over all ranks (x itself without a process group)."""
+    if dist_mod is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(world: int, solves_per_rank: int, max_ms: float) -> float:
+    """Whole-job solves per second: every rank's solves over the slowest rank's time."""
+    return world * solves_per_rank / (max_ms / 1000.0)
+
+
 def roof_source_hash():
     import hashlib
     with open(os.path.join(ROOT, ROOF_SRC[0])) as f:
@@ -194,9 +216,8 @@ def run_ours(args, rank, world):
     n = args.n
     stream = torch.cuda.Stream()
     # one solver per sweep cell owned by this rank, inputs resident in HBM
-    cells = [c for c in range(9) if c % world == rank] or [rank % 9]
-    if args.cells:  # fewer solvers (smaller device footprint, e.g. for profiler captures)
-        cells = cells[:args.cells]
+    # args.cells > 0: fewer solvers (smaller device footprint, e.g. for profiler captures)
+    cells = rank_cells(rank, world, args.cells)
     solvers, yds, yd_host = {}, {}, {}
     for c in cells:
         wl = W.workload_c2(n=n, cell=c)
@@ -247,12 +268,10 @@ def run_ours(args, rank, world):
                 ev[k][1].record(stream)
             t1.record(stream)
         torch.cuda.synchronize()
-        launches = ipm.launch_count() - l0
-        total_ms = t0.elapsed_time(t1)
         if dist:
-            tt = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            total_ms = float(tt.item())
+            dist.barrier()
+        launches = ipm.launch_count() - l0
+        total_ms = max_over_ranks(t0.elapsed_time(t1), dist, "cuda")
         lat = [a.elapsed_time(b) for a, b in ev]
         prof = None
         if profile:
@@ -271,7 +290,7 @@ def run_ours(args, rank, world):
         tot_mx, lat_mx, reps_mx, launches, _ = timed(ipm.PREC_MIXED, args.steps, warm)
     clocks = clk.summary()
     if args.legs == "mixed":  # the timed leg only (used for kernel launch lists)
-        print(json.dumps({"metric": METRIC, "value": world * args.steps / (tot_mx / 1000.0),
+        print(json.dumps({"metric": METRIC, "value": throughput(world, args.steps, tot_mx),
                           "unit": "solves/s", "legs": "mixed", "gpu_launches": launches}))
         return
     # dominant kernel: finest-level multigrid smoothing launches timed by CUDA events on the
@@ -283,7 +302,7 @@ def run_ours(args, rank, world):
     tot_e2e, lat_e2e, _, _, _ = timed(ipm.PREC_MIXED, max(1, min(args.steps, 5)), 1, e2e=True)
 
     K = args.steps
-    value = world * K / (tot_mx / 1000.0)
+    value = throughput(world, K, tot_mx)
     pct = lambda xs, q: float(np.percentile(np.asarray(xs), q))
     hbm, peak_kind = measured_peaks()
     roof = None
@@ -314,13 +333,13 @@ def run_ours(args, rank, world):
         "krylov_iters_per_ipm": statistics.mean(r["krylov_iters_total"] / max(r["ipm_iters"], 1)
                                                 for r in reps_mx),
         "kkt_rel_max": kkt_max,
-        "fp64": {"value": world * fp64_steps / (tot_64 / 1000.0), "ms_per_step": tot_64 / fp64_steps,
+        "fp64": {"value": throughput(world, fp64_steps, tot_64), "ms_per_step": tot_64 / fp64_steps,
                  "ipm_iters": statistics.mean(r["ipm_iters"] for r in reps_64),
                  "krylov_iters_per_ipm": statistics.mean(r["krylov_iters_total"] / max(r["ipm_iters"], 1)
                                                          for r in reps_64),
                  "steps": fp64_steps, "latency_ms": {"p50": pct(lat_64, 50), "p99": pct(lat_64, 99)},
                  "kkt_rel_max": max(r["kkt_rel"] for r in reps_64)},
-        "e2e": {"value": world * len(lat_e2e) / (tot_e2e / 1000.0), "unit": "solves/s",
+        "e2e": {"value": throughput(world, len(lat_e2e), tot_e2e), "unit": "solves/s",
                 "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8},
         "gpu_launches": launches,
         "roofline": roof,
