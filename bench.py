@@ -33,8 +33,8 @@ METRIC = "IPM solves/s & p50/p99 latency, mixed vs FP64 GPU at 1e-6 rel. KKT res
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, profiles/ summary named
 # below), valid while the kernel's source region is unchanged (hash checked at run time).
 ROOF_KERNEL = "k_mg2_pre_restrict_rb<52,52,5,16> (finest level: 5 Jacobi sweeps + residual + restriction)"
-ROOF_TRAFFIC = {"bytes": 8409856,
-                "sha256": "812f5b76b24b3d1dca818a923143d0507f1bdce33a2a6c15c11e1c96afee3d30",
+ROOF_TRAFFIC = {"bytes": 8406272,
+                "sha256": "9a64e0b6708af13123b538ab508c4a54c6378464e9457538b8c4224f88750625",
                 "profile": "profiles/mg2_pre_restrict_rb_1025_full.md"}
 ROOF_SRC = ("paper_1806_05896_gb300/csrc/k_mg_fused.cu",
             "// Register-blocked FP32 tile kernels",

@@ -189,8 +189,8 @@ __global__ void __launch_bounds__(512) k_mg2_prolong_post(GridDesc g, GridDesc g
 }
 
 // ---------------------------------------------------------------------------
-// Register-blocked FP32 tile kernels (same cycle pieces and arithmetic as the two
-// kernels above, laid out for the shared-memory pipe).
+// Register-blocked FP32 tile kernels (same cycle pieces as the two kernels above, laid
+// out for the shared-memory pipe; the stiffness stencil is evaluated on differences).
 //
 // Thread (lane, warp w) owns the tile nodes in columns 1 + lane + 32c (c < CX) and rows
 // 1 + wK + r (r < K). The right-hand side, the diagonal m and the Jacobi weight of its
@@ -287,10 +287,9 @@ IPM_D void rb_pass(const float* __restrict__ cur, float* __restrict__ nxt,
     if (lx > SX - 2) continue;
     const float* col = cur + lx;
     const float* q = col + (ly0 - 1) * SX;
-    float hp = (q[-1] + q[0]) + q[1];
+    float pl = q[-1], pc = q[0], pr = q[1];  // row above
     q = col + ly0 * SX;
-    float xc = q[0];
-    float hc = (q[-1] + xc) + q[1];
+    float cl = q[-1], xc = q[0], cr = q[1];  // this row
     const int gx = X0 - H + lx;
     const bool out_col = MODE != kRBSweep && lx >= H && lx < H + TX && gx <= g.n - 2;
 #pragma unroll
@@ -298,10 +297,13 @@ IPM_D void rb_pass(const float* __restrict__ cur, float* __restrict__ nxt,
       const int ly = ly0 + r;
       if (K * NW > SY - 2 && ly > SY - 2) break;
       q = col + (ly + 1) * SX;
-      const float xn = q[0];
-      const float hn = (q[-1] + xn) + q[1];
-      const float box = (hp + hc) + hn;
-      const float ax = (3.0f * xc - box * float(1.0 / 3.0)) + rm[c][r] * xc;
+      const float nl = q[-1], xn = q[0], nr = q[1];  // row below
+      // stiffness part as (1/3) sum over the 8 neighbours of (x_c - x_nb): the difference of
+      // neighbouring values of a smooth field is exact in FP32 (Sterbenz), so this keeps
+      // about 1/h more digits than 8 x_c - (sum of the 8) on fine grids
+      const float s8 = (((xc - pl) + (xc - pc)) + ((xc - pr) + (xc - cl))) +
+                       (((xc - cr) + (xc - nl)) + ((xc - xn) + (xc - nr)));
+      const float ax = s8 * float(1.0 / 3.0) + rm[c][r] * xc;
       const int gy = Y0 - H + ly;
       const bool out = out_col && ly >= H && ly < H + TY && gy <= g.n - 2;
       if (MODE == kRBResidual) {
@@ -312,9 +314,12 @@ IPM_D void rb_pass(const float* __restrict__ cur, float* __restrict__ nxt,
         if (MODE == kRBSweep) nxt[ly * SX + lx] = v;
         else if (out) xout[(long long)gy * g.pitch + gx] = v;
       }
-      hp = hc;
-      hc = hn;
+      pl = cl;
+      pc = xc;
+      pr = cr;
+      cl = nl;
       xc = xn;
+      cr = nr;
     }
   }
 }

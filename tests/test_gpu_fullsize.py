@@ -57,7 +57,9 @@ def test_mixed_vcycle_tile_kernels(n):
     v_o64 = host(s.vcycle(False, md, bd, out, precision=ipm.PREC_MIXED, kernel_flags=16))[qp.idx]
     v64 = host(s.vcycle(False, md, bd, out))[qp.idx]
     s.close()
-    assert rel(v, v_sweep) < 2e-6
+    # the per-sweep FP32 kernels take the stiffness stencil as 8 x_c - (sum of 8), the fused
+    # ones on differences (x_c - x_nb): both within FP32 reach of the FP64 cycles
+    assert rel(v, v_sweep) < 1e-5
     assert rel(v, v_o64) < 2e-6  # float-float vs FP64 outer residual
     assert rel(v, v64) < 1e-5
     assert np.linalg.norm(b - A @ v) < 0.05 * np.linalg.norm(b)
@@ -96,7 +98,7 @@ def test_mixed_preconditioner_tile_kernels(n):
     for a, b in ((zi, zs), (zi, z64)):
         for k in range(4):
             blk = slice(k * nI, (k + 1) * nI)
-            assert rel(a[blk], b[blk]) < (2e-6 if b is zs else 1e-5)
+            assert rel(a[blk], b[blk]) < 1e-5
 
 
 def test_newton_apply_full_size(full):
