@@ -1,5 +1,5 @@
 // Convection-diffusion operator with SUPG (Section 5.2) as a stored 9-point stencil per
-// node, and Galerkin coarse-grid operators P^T L P for the multigrid hierarchy.
+// node (assembled on every multigrid level with that level's mesh size).
 //
 // L = eps K + N + S on Q1 elements of the unit square:
 //   K_e[a,b] = int grad phi_b . grad phi_a,     N_e[a,b] = int (w . grad phi_b) phi_a,
@@ -79,44 +79,6 @@ __global__ void k_cd_coef(GridDesc g, double eps, double* __restrict__ coef) {
   for (int o = 0; o < 9; ++o) coef[(long long)o * g.field + c] = acc[o];
 }
 
-IPM_D bool interior2(int i, int j, int n) { return i >= 1 && i <= n - 2 && j >= 1 && j <= n - 2; }
-
-// coarse stencil of P^T L P at coarse node (I, J); P bilinear with weights 1, 1/2, 1/4
-__global__ void k_galerkin(GridDesc gf, GridDesc gc, const double* __restrict__ cf,
-                           double* __restrict__ cc) {
-  int I, J, K;
-  long long c;
-  if (!interior_node(gc, I, J, K, c)) return;
-  double acc[9];
-  for (int o = 0; o < 9; ++o) acc[o] = 0.0;
-  const int nf = gf.n, ncn = gc.n;
-  for (int di = -1; di <= 1; ++di)
-    for (int dj = -1; dj <= 1; ++dj) {
-      const int fi = 2 * I + di, fj = 2 * J + dj;  // fine row i, weight P[i, I]
-      if (!interior2(fi, fj, nf)) continue;
-      const double wi = (di ? 0.5 : 1.0) * (dj ? 0.5 : 1.0);
-      const long long ci = node_index(gf, fi, fj, 0);
-      for (int o = 0; o < 9; ++o) {
-        const int gi = fi + (o % 3 - 1), gj = fj + (o / 3 - 1);  // fine column j
-        if (!interior2(gi, gj, nf)) continue;
-        const double lij = cf[(long long)o * gf.field + ci];
-        if (lij == 0.0) continue;
-        // coarse parents of fine node (gi, gj) with interpolation weights
-        const int px0 = gi >> 1, py0 = gj >> 1;
-        const int npx = (gi & 1) ? 2 : 1, npy = (gj & 1) ? 2 : 1;
-        const double wpx = npx == 2 ? 0.5 : 1.0, wpy = npy == 2 ? 0.5 : 1.0;
-        for (int qy = 0; qy < npy; ++qy)
-          for (int qx = 0; qx < npx; ++qx) {
-            const int PX = px0 + qx, PY = py0 + qy;
-            if (!interior2(PX, PY, ncn)) continue;
-            const int ox = PX - I, oy = PY - J;
-            acc[(oy + 1) * 3 + (ox + 1)] += wi * lij * wpx * wpy;
-          }
-      }
-    }
-  for (int o = 0; o < 9; ++o) cc[(long long)o * gc.field + c] = acc[o];
-}
-
 __global__ void k_to_float(long long n, const double* __restrict__ x, float* __restrict__ y) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
@@ -128,12 +90,6 @@ __global__ void k_to_float(long long n, const double* __restrict__ x, float* __r
 void launch_cd_coef(const GridDesc& g, double eps, double* coef, cudaStream_t s) {
   count_launches(1);
   k_cd_coef<<<interior_grid(g), interior_block(), 0, s>>>(g, eps, coef);
-}
-
-void launch_galerkin(const GridDesc& gf, const GridDesc& gc, const double* cf, double* cc,
-                     cudaStream_t s) {
-  count_launches(1);
-  k_galerkin<<<interior_grid(gc), interior_block(), 0, s>>>(gf, gc, cf, cc);
 }
 
 void launch_to_float(long long n, const double* x, float* y, cudaStream_t s) {

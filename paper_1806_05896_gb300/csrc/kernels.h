@@ -175,11 +175,9 @@ void launch_cheb2_block(const GridDesc& g, const ChebSteps& cs, const Ti* b, con
                         int first, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
-// k_cd.cu (convection-diffusion + SUPG stencil, Galerkin coarse operators)
+// k_cd.cu (convection-diffusion + SUPG stencil per level)
 // ----------------------------------------------------------------------------
 void launch_cd_coef(const GridDesc& g, double eps, double* coef, cudaStream_t s);
-void launch_galerkin(const GridDesc& gf, const GridDesc& gc, const double* cf, double* cc,
-                     cudaStream_t s);
 void launch_to_float(long long n, const double* x, float* y, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
