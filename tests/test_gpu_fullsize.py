@@ -40,8 +40,8 @@ def full():
 @pytest.mark.parametrize("n", [129, 257, 513, 1025])
 def test_mixed_vcycle_tile_kernels(n):
     """Mixed-precision V-cycles (FP32 tile kernels, float-float outer residual and iterate):
-    the fused tiled kernels give the per-sweep kernels' result, the float-float outer step
-    the FP64 one's, both agree with the FP64 cycles to FP32 accuracy and contract the
+    the fused tiled kernels agree with the per-sweep kernels and the FP64 cycles to FP32
+    accuracy, the float-float outer step with the FP64 one, and the cycles contract the
     error of (L + diag m) x = b for the oracle's operator."""
     torch = torch_cuda()
     qp = Q.build(2, n, 1e-2, 1e-3, -2.0, 1.5)
@@ -73,7 +73,7 @@ def test_mixed_vcycle_tile_kernels(n):
 def test_mixed_preconditioner_tile_kernels(n):
     """P_T^{-1} r in mixed precision (FP32 Chebyshev and V-cycle tile kernels): the y-block
     is the oracle's 20-step Chebyshev to FP32 accuracy, the (w, v)-block the FP64 path's
-    to FP32 accuracy, and the fused kernels give the per-sweep kernels' result."""
+    to FP32 accuracy, and the fused kernels agree with the per-sweep ones to FP32 accuracy."""
     torch = torch_cuda()
     qp = Q.build(2, n, 1e-2, 1e-3, -2.0, 1.5)
     rng = np.random.default_rng(n + 1)
