@@ -15,6 +15,7 @@
 //
 // A V-cycle on a 1025^2 grid thus takes 2 launches per level above the coarse
 // block plus one, instead of about 14 per level.
+#include <mutex>
 #include <type_traits>
 
 #include "kernels.h"
@@ -536,9 +537,13 @@ size_t tile_smem(int halo, int tx, int ty) {
   return 5 * (size_t)(tx + 2 * halo) * (ty + 2 * halo) * sizeof(T);
 }
 
-// raise a kernel's dynamic shared memory limit when a launch needs more than the default
+// raise a kernel's dynamic shared memory limit when a launch needs more than the default;
+// the limit only grows, under a lock (solvers on several host threads launch concurrently)
+std::mutex g_smem_attr_mu;
 void ensure_smem_attr(const void* fn, size_t bytes, size_t& set_to) {
-  if (bytes > 48 * 1024 && bytes > set_to) {
+  if (bytes <= 48 * 1024) return;
+  std::lock_guard<std::mutex> lk(g_smem_attr_mu);
+  if (bytes > set_to) {
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     set_to = bytes;
   }
