@@ -930,7 +930,17 @@ struct ipm_solver {
       cudaGraph_t graph = nullptr;
       long long before = launches_total();
       CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-      arnoldi_body(o, j, stride, len, tri);
+      try {
+        arnoldi_body(o, j, stride, len, tri);
+      } catch (...) {
+        // leave the stream usable: end (and drop) the partial capture, then report
+        cudaGraph_t partial = nullptr;
+        cudaStreamEndCapture(stream, &partial);
+        if (partial) cudaGraphDestroy(partial);
+        cudaGetLastError();
+        count_launches(before - launches_total());
+        throw;
+      }
       CK(cudaStreamEndCapture(stream, &graph));
       // captured launches do not run now: count them at each replay instead
       gcount.resize(j + 1, 0);
