@@ -221,7 +221,9 @@ int ipm_server_submit(ipm_server* sv, const ipm_request* rq, long long* ticket);
 int ipm_server_wait(ipm_server* sv, long long ticket, ipm_report* rep, double* u, size_t len,
                     double* latency_s, double* queue_s);
 int ipm_server_stats(ipm_server* sv, size_t* bytes_in_use, int* solvers, long long* completed);
-/* Stop the workers (after the running solves) and free every pooled solver. */
+/* Stop the workers (after the running solves) and free every pooled solver. Queued
+ * requests that have not started are dropped with their tickets: call it only when no
+ * thread is blocked in, or will still call, ipm_server_wait. */
 void ipm_server_destroy(ipm_server* sv);
 
 /* ---------------------------------------------------------------------------
