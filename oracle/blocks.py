@@ -1,7 +1,8 @@
 """Dense block matrices of Section 4 (tiny grids only) and Chebyshev semi-iteration.
 
 Saddle-point form of (NewtonSystem): calA = [[A, B^T], [B, 0]] with
-  A = blkdiag(M + Theta_y, alpha M~ + Theta_z),   B = [L, -M, M]   (z = [w; v]),
+  A = blkdiag(M + Theta_y, alpha M~ + Theta_z),   B = [L, -M, M]   (z = [w; v];
+  under partial observation the (1,1) block holds the observed mass M_s instead of M),
 negative Schur complement S = B A^{-1} B^T, ideal preconditioners
 P_1 = blkdiag(A, S), P_2 = [[A, 0], [B, -S]] and the practical
 P_D = blkdiag(A_hat, S_hat), P_T = [[A_hat, 0], [B, -S_hat]] with
@@ -31,7 +32,7 @@ def blocks(qp: QP, th_y, th_w, th_v):
     a = qp.alpha
     n = qp.nI
     A = np.zeros((3 * n, 3 * n))
-    A[:n, :n] = M + np.diag(th_y)
+    A[:n, :n] = dense(qp.Mcost) + np.diag(th_y)
     A[n:2 * n, n:2 * n] = a * M + np.diag(th_w)
     A[n:2 * n, 2 * n:] = -a * M
     A[2 * n:, n:2 * n] = -a * M

@@ -3,7 +3,8 @@
 Plain definition, no interior point machinery: eliminate the state through the
 state equation L y = M u + f, y(u) = G u + y0 with G = L^{-1} M, y0 = L^{-1} f,
 and minimise the strictly convex reduced objective
-  J(u) = 1/2 y(u)^T M y(u) - y(u)^T c_y + alpha/2 u^T M u + beta ||D u||_1
+  J(u) = 1/2 y(u)^T M_c y(u) - y(u)^T c_y + alpha/2 u^T M u + beta ||D u||_1
+(M_c the tracking mass: M, or the observed subdomain's mass under partial observation)
 over the box u_a <= u <= u_b by cyclic coordinate descent with exact
 one-dimensional minimisation (soft threshold, then clip). The result is
 certified by the subgradient optimality conditions.
@@ -20,10 +21,11 @@ def reduced_qp(qp: QP):
     """Hessian H, linear term q of the smooth part of J, and (G, y0)."""
     L = qp.L.toarray()
     M = qp.M.toarray()
+    Mc = qp.Mcost.toarray()
     G = np.linalg.solve(L, M)
     y0 = np.linalg.solve(L, qp.fvec)
-    H = G.T @ M @ G + qp.alpha * M
-    q = G.T @ (M @ y0 - qp.cy)
+    H = G.T @ Mc @ G + qp.alpha * M
+    q = G.T @ (Mc @ y0 - qp.cy)
     return H, q, G, y0
 
 
@@ -54,7 +56,7 @@ def solve(qp: QP, ua: np.ndarray, ub: np.ndarray, tol: float = 1e-15,
             break
     y = G @ u + y0
     Lt = qp.L.toarray().T
-    p = -np.linalg.solve(Lt, qp.M @ y - qp.cy)
+    p = -np.linalg.solve(Lt, qp.Mcost @ y - qp.cy)
     return y, u, p, sweep + 1
 
 

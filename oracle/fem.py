@@ -120,6 +120,19 @@ def poisson_matrices(dim: int, n: int):
     return K, M
 
 
+def mass_subdomain(dim: int, n: int, inside) -> sp.csr_matrix:
+    """Full-grid Q1 mass over the elements whose centre satisfies ``inside(centres)``
+    (centres: (n_elem, dim) array -> boolean mask), the observation mass of the
+    partial-observation problem."""
+    h = 1.0 / (n - 1)
+    phi, _, wq, _ = q1_basis(dim, gauss01(2))
+    Me = np.einsum("q,aq,bq->ab", wq, phi, phi) * h ** dim
+    conn = element_connectivity(dim, n)
+    mask = np.asarray(inside(element_origins(dim, n) + 0.5 * h), dtype=bool)
+    local = np.broadcast_to(Me, (conn.shape[0],) + Me.shape) * mask[:, None, None]
+    return _scatter(conn, local, n ** dim)
+
+
 def paper_wind(x, y):
     """Recirculating wind of Section 5.2: w = (2 x2 (1 - x1^2), -2 x1 (1 - x2^2))."""
     return 2.0 * y * (1.0 - x * x), -2.0 * x * (1.0 - y * y)

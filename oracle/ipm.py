@@ -115,7 +115,7 @@ def gradients(qp: QP, s: State):
     g_p = L y - Mbar z - f."""
     Mu = qp.M @ (s.w - s.v)
     Mp = qp.M @ s.p
-    g_y = qp.M @ s.y - qp.cy + qp.L.T @ s.p
+    g_y = qp.Mcost @ s.y - qp.cy + qp.L.T @ s.p
     g_w = qp.alpha * Mu + qp.beta * qp.d - Mp
     g_v = -qp.alpha * Mu + qp.beta * qp.d + Mp
     g_p = qp.L @ s.y - Mu - qp.fvec
@@ -128,7 +128,7 @@ def newton_matrix(qp: QP, th_y, th_w, th_v) -> sp.csc_matrix:
     M, L = qp.M, qp.L
     D = sp.diags
     return sp.bmat([
-        [M + D(th_y), None, None, L.T],
+        [qp.Mcost + D(th_y), None, None, L.T],
         [None, a * M + D(th_w), -a * M, -M],
         [None, -a * M, a * M + D(th_v), M],
         [L, -M, M, None],

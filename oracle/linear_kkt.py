@@ -17,7 +17,7 @@ from .qp import QP
 
 def solve(qp: QP):
     n = qp.nI
-    K = sp.bmat([[qp.M, None, qp.L.T],
+    K = sp.bmat([[qp.Mcost, None, qp.L.T],
                  [None, qp.alpha * qp.M, -qp.M],
                  [qp.L, -qp.M, None]]).tocsc()
     rhs = np.concatenate([qp.cy, np.zeros(n), qp.fvec])

@@ -47,10 +47,18 @@ class QP:
     fvec: np.ndarray
     yd_full: np.ndarray
     g_full: np.ndarray
+    # partial observation: mass of the observed subdomain in the cost (None = M)
+    Mc: Optional[sp.csr_matrix] = None
+    Mcfull: Optional[sp.csr_matrix] = None
 
     @property
     def nI(self) -> int:
         return self.idx.size
+
+    @property
+    def Mcost(self) -> sp.csr_matrix:
+        """Mass of the tracking term: M, or M_s for partial observation."""
+        return self.M if self.Mc is None else self.Mc
 
     def full(self, x_int: np.ndarray, boundary: Optional[np.ndarray] = None) -> np.ndarray:
         """Embed an interior vector in the full grid (boundary = ``boundary`` or zero)."""
@@ -62,7 +70,8 @@ class QP:
         """Q(y, z): 1/2 ||y_h - y_d,h||^2_{L2} + alpha/2 u^T M u + beta 1^T Dbar z (full-grid state)."""
         e = self.full(y, self.g_full) - self.yd_full
         u = w - v
-        return float(0.5 * e @ (self.Mfull @ e) + 0.5 * self.alpha * u @ (self.M @ u)
+        Mt = self.Mfull if self.Mcfull is None else self.Mcfull
+        return float(0.5 * e @ (Mt @ e) + 0.5 * self.alpha * u @ (self.M @ u)
                      + self.beta * self.d @ (w + v))
 
 
@@ -83,12 +92,15 @@ def split_bounds(ua: np.ndarray, ub: np.ndarray):
 
 def build(dim: int, n: int, alpha: float, beta: float, ua, ub, ya=-math.inf, yb=math.inf,
           yd=None, f=None, g=None, kind: str = "poisson", eps: float = 1.0,
-          supg: bool = True, lump: bool = False) -> QP:
+          supg: bool = True, lump: bool = False, observe=None) -> QP:
     """Assemble the QP for a Q1 grid with ``n`` nodes per direction on the unit square/cube.
 
     ``lump=True`` replaces every mass matrix by the lumped D (row sums), the
     setting of the eigenvalue theorem of Section 4.2 and of the pointwise
-    optimality relation u = P_[ua,ub](sign(p) max(|p| - beta, 0)/alpha)."""
+    optimality relation u = P_[ua,ub](sign(p) max(|p| - beta, 0)/alpha).
+    ``observe``: partial observation (the subsection on partial observations): the
+    tracking term integrates over the elements whose centre satisfies
+    ``observe(centres)``, so the cost mass M_s differs from the coupling mass M."""
     if kind == "poisson":
         Lfull, Mfull = fem.poisson_matrices(dim, n)
     elif kind == "cd":
@@ -121,10 +133,12 @@ def build(dim: int, n: int, alpha: float, beta: float, ua, ub, ya=-math.inf, yb=
     g_lift = g_full.copy()
     g_lift[idx] = 0.0
     g_full = g_lift
-    cy = (Mfull @ (yd_full - g_lift))[idx]
+    Mcfull = None if observe is None else fem.mass_subdomain(dim, n, observe)
+    Mc = None if Mcfull is None else Mcfull[idx][:, idx].tocsr()
+    cy = ((Mfull if Mcfull is None else Mcfull) @ (yd_full - g_lift))[idx]
     fvec = (Mfull @ f_full)[idx] - (Lfull @ g_lift)[idx]
     return QP(dim, n, 1.0 / (n - 1), idx, Lfull, Mfull, L, M, d, dM, float(alpha), float(beta),
-              ya_i, yb_i, za, zb, cy, fvec, yd_full, g_full)
+              ya_i, yb_i, za, zb, cy, fvec, yd_full, g_full, Mc, Mcfull)
 
 
 def from_workload(wl, **kw) -> QP:
