@@ -53,6 +53,25 @@ def test_ipm_matches_brute_force_with_partial_observation():
     assert rel(r.state.p, p_b) < 1e-9
 
 
+def test_ipm_matches_brute_force_with_partial_observation_3d():
+    """The paper's three-dimensional case: observation in 0.2 < x1 < 0.4, 0.4 < x2 < 0.9,
+    all x3 (9^3 grid)."""
+    n = 9
+    x, y, z = W.node_coords(3, n)
+    yd = 20.0 * np.sin(4 * np.pi * (y - 0.4)) * np.sin(np.pi * z)
+    qp = Q.build(3, n, 1e-2, 3e-3, -2.0, 1.5, yd=yd, observe=omega1)
+    N = qp.nI
+    y_b, u_b, p_b, _ = brute.solve(qp, np.full(N, -2.0), np.full(N, 1.5))
+    cert, counts = brute.certificate(qp, u_b, p_b, -2.0, 1.5, 1e-14)
+    assert cert < 1e-15
+    assert all(c > 0 for c in counts.values()), counts
+    r = oipm.solve(qp, n_iter=22)
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+    assert rel(r.u(), u_b) < 1e-7
+    assert rel(r.state.y, y_b) < 1e-8
+    assert rel(r.state.p, p_b) < 1e-9
+
+
 def _late_thetas(qp, k=7):
     r = oipm.solve(qp, n_iter=k)
     return oipm.thetas(qp, r.state)
