@@ -542,8 +542,3 @@ void launch_to_float2(const GridDesc& g, const double* a, const double* b, float
   count_launches(1);
   k_to_float2<<<interior_grid(g), interior_block(), 0, s>>>(g, a, b, a32, b32);
 }
-void launch_reduce_cols(const double* part, long long nrows, int ncols, double* out,
-                        cudaStream_t s) {
-  count_launches(1);
-  k_reduce_cols<<<ncols, 256, 0, s>>>(part, nrows, ncols, out);
-}

@@ -54,27 +54,11 @@ __global__ void k_axpy_multi(double* __restrict__ w, const double* __restrict__ 
   }
 }
 
-__global__ void k_scale(double* __restrict__ y, const double* __restrict__ x,
-                        const double* __restrict__ s, int invert, long long len) {
-  double f = invert ? 1.0 / s[0] : s[0];
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
-       e += (long long)gridDim.x * blockDim.x)
-    y[e] = x[e] * f;
-}
-
 __global__ void k_axpby(double* y, const double* x, double a, double b,
                         long long len) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
        e += (long long)gridDim.x * blockDim.x)
     y[e] = b == 0.0 ? a * x[e] : a * x[e] + b * y[e];  // b = 0 never reads y
-}
-
-__global__ void k_axpy_dev(double* __restrict__ y, const double* __restrict__ x,
-                           const double* __restrict__ a, double sign, long long len) {
-  double f = sign * a[0];
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
-       e += (long long)gridDim.x * blockDim.x)
-    y[e] += f * x[e];
 }
 
 int vec_blocks(long long len) {
@@ -99,20 +83,9 @@ void launch_axpy_multi(double* w, const double* V, long long stride, int nv, con
   count_launches(1);
   k_axpy_multi<<<vec_blocks(len), 256, 0, s>>>(w, V, stride, nv, coef, sign, len);
 }
-void launch_scale(double* y, const double* x, const double* num, const double* den, int invert,
-                  long long len, cudaStream_t s) {
-  (void)num;
-  count_launches(1);
-  k_scale<<<vec_blocks(len), 256, 0, s>>>(y, x, den, invert, len);
-}
 void launch_axpby(double* y, const double* x, double a, double b, long long len, cudaStream_t s) {
   count_launches(1);
   k_axpby<<<vec_blocks(len), 256, 0, s>>>(y, x, a, b, len);
-}
-void launch_axpy_dev(double* y, const double* x, const double* a, double sign, long long len,
-                     cudaStream_t s) {
-  count_launches(1);
-  k_axpy_dev<<<vec_blocks(len), 256, 0, s>>>(y, x, a, sign, len);
 }
 void launch_dot(const double* a, const double* b, long long len, double* part, double* out,
                 cudaStream_t s) {

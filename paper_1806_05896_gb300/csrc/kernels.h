@@ -68,8 +68,6 @@ void launch_newton_apply(const GridDesc& g, const IpmProblem& pb, const IpmDiag&
 // same operator, output as a float-float Krylov vector (high parts, then low parts)
 void launch_newton_apply_ff(const GridDesc& g, const IpmProblem& pb, const IpmDiag& dg,
                             const double* x, float* y, cudaStream_t s);
-void launch_reduce_cols(const double* part, long long nrows, int ncols, double* out,
-                        cudaStream_t s);
 long long interior_blocks(const GridDesc& g);
 
 // ----------------------------------------------------------------------------
@@ -199,11 +197,7 @@ void launch_multidot(const double* V, long long stride, int nv, const double* w,
                      double* part, double* out, cudaStream_t s);
 void launch_axpy_multi(double* w, const double* V, long long stride, int nv, const double* coef,
                        double sign, long long len, cudaStream_t s);
-void launch_scale(double* y, const double* x, const double* num, const double* den, int invert,
-                  long long len, cudaStream_t s);
 void launch_axpby(double* y, const double* x, double a, double b, long long len, cudaStream_t s);
-void launch_axpy_dev(double* y, const double* x, const double* a, double sign, long long len,
-                     cudaStream_t s);
 void launch_dot(const double* a, const double* b, long long len, double* part, double* out,
                 cudaStream_t s);
 void launch_scale_rsqrt(double* y, const double* x, const double* s, long long len,
