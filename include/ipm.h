@@ -277,10 +277,13 @@ int ipm_newton_step_device(ipm_solver* s, const ipm_options* opt, const double* 
  * x fastest); x gets a zero boundary and must not alias theta_y or b. Work is
  * enqueued on `stream` (NULL = legacy default stream).
  * Work vectors live in one fixed device array of 3 * 274625 doubles (6.3 MiB)
- * that every GPU loading the library keeps until the process exits; grids with
- * n^dim > 274625 (beyond 65^3, 513^2) are rejected with IPM_EINVAL. The first
- * call on a device looks up that array's device address (cudaGetSymbolAddress)
- * with the device current; make that first call before any stream capture.
+ * that every GPU loading the library keeps until the process exits (with lazy
+ * module loading, the default, the array is materialised on a device by the
+ * first call there, not at library load); grids with n^dim > 274625 (beyond
+ * 65^3, 513^2) are rejected with IPM_EINVAL. The first call on a device (and
+ * the first after a device reset) looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.
  * All calls share the array and each clears the part it uses: calls that overlap
  * on the GPU (different streams, or host threads racing) corrupt each other.
  * No cudaMalloc, cudaFree or allocating library routine is called. */

@@ -259,7 +259,7 @@ def solve(qp: QP, sigma: float = 0.2, alpha0: float = 0.995, mu0: float = 1.0,
           eps_p: float = 1e-6, eps_d: float = 1e-6, eps_c: float = 1e-6,
           stop: str = "paper", kkt_tol: float = 1e-6, max_iter: int = 200,
           n_iter: Optional[int] = None, refine: int = 2, mu_rule: str = "schedule",
-          common_step: bool = False) -> Result:
+          common_step: bool = False, newton_solve=None) -> Result:
     """Run Algorithm A.1.
 
     stop = "paper": ||xi_p|| <= eps_p and ||xi_d|| <= eps_d and ||xi_c|| <= eps_c;
@@ -271,6 +271,9 @@ def solve(qp: QP, sigma: float = 0.2, alpha0: float = 0.995, mu0: float = 1.0,
                           iterate), the duality-measure form of the path-following scheme
                           the paper cites; it equals the schedule while full steps are taken.
     common_step = True:   both primal and dual variables move with min(alpha_P, alpha_D).
+    newton_solve:         None = the sparse direct solve (direct tier); else a callable
+                          (qp, A, b, Theta_y, Theta_w, Theta_v) -> dx, e.g. the iterative
+                          tier's FGMRES + P_T (``oracle.iterative.newton_solver``).
     """
     n = qp.nI
     s = initial_state(qp, mu0)
@@ -301,7 +304,10 @@ def solve(qp: QP, sigma: float = 0.2, alpha0: float = 0.995, mu0: float = 1.0,
         th_y, th_w, th_v = thetas(qp, s)
         A = newton_matrix(qp, th_y, th_w, th_v)
         b = newton_rhs(qp, s, mu)
-        dx = solve_direct(A, b, refine)
+        if newton_solve is None:
+            dx = solve_direct(A, b, refine)
+        else:
+            dx = newton_solve(qp, A, b, th_y, th_w, th_v)
         dy, dw, dv, dp = dx[:n], dx[n:2 * n], dx[2 * n:3 * n], dx[3 * n:]
         dl = multiplier_steps(qp, s, dy, dw, dv, mu)
         aP = min(max_step(s.y, dy, qp.ya, qp.yb),

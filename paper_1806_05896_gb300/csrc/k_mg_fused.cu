@@ -15,6 +15,7 @@
 //
 // A V-cycle on a 1025^2 grid thus takes 2 launches per level above the coarse
 // block plus one, instead of about 14 per level.
+#include <map>
 #include <mutex>
 #include <type_traits>
 
@@ -537,16 +538,23 @@ size_t tile_smem(int halo, int tx, int ty) {
   return 5 * (size_t)(tx + 2 * halo) * (ty + 2 * halo) * sizeof(T);
 }
 
-// raise a kernel's dynamic shared memory limit when a launch needs more than the default;
-// the limit only grows, under a lock (solvers on several host threads launch concurrently)
+// raise a kernel's dynamic shared memory limit when a launch needs more than the default.
+// The attribute is per device, so the raised limit is remembered per (kernel, device); it
+// only grows, under a lock (solvers on several host threads launch concurrently). A failed
+// cudaFuncSetAttribute is not remembered: the launch that follows then fails, and the
+// solver's next error check reports IPM_ECUDA.
 std::mutex g_smem_attr_mu;
-void ensure_smem_attr(const void* fn, size_t bytes, size_t& set_to) {
+std::map<std::pair<const void*, int>, size_t> g_smem_attr_set;
+void ensure_smem_attr(const void* fn, size_t bytes) {
   if (bytes <= 48 * 1024) return;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
   std::lock_guard<std::mutex> lk(g_smem_attr_mu);
-  if (bytes > set_to) {
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  size_t& set_to = g_smem_attr_set[{fn, dev}];
+  if (bytes > set_to &&
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+          cudaSuccess)
     set_to = bytes;
-  }
 }
 
 }  // namespace
@@ -564,9 +572,8 @@ template <typename T, int TX, int TY>
 void pre_restrict_tiles(const GridDesc& g, const GridDesc& gc, const T* xin, T* xout, const T* b,
                         const T* m, T* bc, double omega, int nu, int zero_init, int threads,
                         cudaStream_t s) {
-  static size_t set_to = 0;
   size_t sm = tile_smem<T>(nu + 2, TX, TY);
-  ensure_smem_attr((const void*)k_mg2_pre_restrict<T, TX, TY>, sm, set_to);
+  ensure_smem_attr((const void*)k_mg2_pre_restrict<T, TX, TY>, sm);
   dim3 grid((g.n + TX - 1) / TX, (g.n + TY - 1) / TY);
   count_launches(1);
   k_mg2_pre_restrict<T, TX, TY><<<grid, threads, sm, s>>>(g, gc, xin, xout, b, m, bc, (T)omega, nu,
@@ -578,9 +585,8 @@ void pre_restrict_rb(const GridDesc& g, const GridDesc& gc, const float* xin, fl
                      const float* b, const float* m, float* bc, double omega, int zero_init,
                      cudaStream_t s) {
   constexpr int NU = kRBSweeps;
-  static size_t set_to = 0;
   const size_t sm = RBShape<TX, TY, NU + 2, NW>::smem;
-  ensure_smem_attr((const void*)k_mg2_pre_restrict_rb<TX, TY, NU, NW>, sm, set_to);
+  ensure_smem_attr((const void*)k_mg2_pre_restrict_rb<TX, TY, NU, NW>, sm);
   dim3 grid((g.n - 2 + TX - 1) / TX, (g.n - 2 + TY - 1) / TY);
   count_launches(1);
   k_mg2_pre_restrict_rb<TX, TY, NU, NW><<<grid, NW * 32, sm, s>>>(g, gc, xin, xout, b, m, bc,
@@ -591,9 +597,8 @@ template <int TX, int TY, int NW>
 void prolong_post_rb(const GridDesc& g, const GridDesc& gc, const float* xin, const float* xc,
                      float* xout, const float* b, const float* m, double omega, cudaStream_t s) {
   constexpr int NU = kRBSweeps;
-  static size_t set_to = 0;
   const size_t sm = RBShape<TX, TY, NU, NW>::smem;
-  ensure_smem_attr((const void*)k_mg2_prolong_post_rb<TX, TY, NU, NW>, sm, set_to);
+  ensure_smem_attr((const void*)k_mg2_prolong_post_rb<TX, TY, NU, NW>, sm);
   dim3 grid((g.n - 2 + TX - 1) / TX, (g.n - 2 + TY - 1) / TY);
   count_launches(1);
   k_mg2_prolong_post_rb<TX, TY, NU, NW><<<grid, NW * 32, sm, s>>>(g, gc, xin, xc, xout, b, m,
@@ -623,9 +628,8 @@ template <typename T, int TX, int TY>
 void prolong_post_tiles(const GridDesc& g, const GridDesc& gc, const T* xin, const T* xc, T* xout,
                         const T* b, const T* m, double omega, int nu, int threads,
                         cudaStream_t s) {
-  static size_t set_to = 0;
   size_t sm = tile_smem<T>(nu, TX, TY);
-  ensure_smem_attr((const void*)k_mg2_prolong_post<T, TX, TY>, sm, set_to);
+  ensure_smem_attr((const void*)k_mg2_prolong_post<T, TX, TY>, sm);
   dim3 grid((g.n + TX - 1) / TX, (g.n + TY - 1) / TY);
   count_launches(1);
   k_mg2_prolong_post<T, TX, TY><<<grid, threads, sm, s>>>(g, gc, xin, xc, xout, b, m, (T)omega,
@@ -650,9 +654,8 @@ void launch_mg2_prolong_post(const GridDesc& g, const GridDesc& gc, const T* xin
 template <typename T>
 void launch_mg2_coarse(const MGCoarse<T>& cl, const T* btop, T* xtop, double omega, int nu_pre,
                        int nu_post, int load_x, cudaStream_t s) {
-  static size_t set_to = 0;
   size_t sm = mg2_coarse_smem(cl);
-  ensure_smem_attr((const void*)k_mg2_coarse<T>, sm, set_to);
+  ensure_smem_attr((const void*)k_mg2_coarse<T>, sm);
   count_launches(1);
   k_mg2_coarse<T><<<1, 1024, sm, s>>>(cl, btop, xtop, (T)omega, nu_pre, nu_post, load_x);
 }
@@ -896,9 +899,8 @@ template <int TX, int TY, int NS, int NW, typename Ti>
 void cheb2_rb(const GridDesc& g, const ChebSteps& cs, const Ti* b, const float* thy,
               const float* xc_in, const float* xp_in, float* xc_out, float* xp_out,
               double* final_out, float* final32, int first, cudaStream_t s) {
-  static size_t set_to = 0;
   const size_t sm = RBShape<TX, TY, NS, NW>::smem;
-  ensure_smem_attr((const void*)k_cheb2_rb<TX, TY, NS, NW, Ti>, sm, set_to);
+  ensure_smem_attr((const void*)k_cheb2_rb<TX, TY, NS, NW, Ti>, sm);
   dim3 grid((g.n - 2 + TX - 1) / TX, (g.n - 2 + TY - 1) / TY);
   count_launches(1);
   k_cheb2_rb<TX, TY, NS, NW, Ti><<<grid, NW * 32, sm, s>>>(g, cs, b, thy, xc_in, xp_in, xc_out,
@@ -937,9 +939,8 @@ void launch_cheb2_block(const GridDesc& g, const ChebSteps& cs, const Ti* b, con
       return;
     }
   }
-  static size_t set_to = 0;
   size_t sm = 6 * (size_t)(FTX + 2 * cs.ns) * (FTY + 2 * cs.ns) * sizeof(T);
-  ensure_smem_attr((const void*)k_cheb2_block<T, Ti, To>, sm, set_to);
+  ensure_smem_attr((const void*)k_cheb2_block<T, Ti, To>, sm);
   dim3 grid((g.n + FTX - 1) / FTX, (g.n + FTY - 1) / FTY);
   count_launches(1);
   k_cheb2_block<T, Ti, To><<<grid, 512, sm, s>>>(g, cs, b, thy, xc_in, xp_in, xc_out, xp_out,

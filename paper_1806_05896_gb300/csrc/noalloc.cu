@@ -6,6 +6,7 @@
 // may imply) would stall other work. This entry point keeps its work vectors in
 // one file-scope device array of fixed size instead; every GPU that loads the
 // library holds that array until the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -24,24 +25,65 @@ static __device__ __align__(256) double g_cheb_scratch[3 * kNoAllocMaxNodes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-double* g_scratch_addr[kMaxDevices] = {};
+struct Cached {
+  double* addr = nullptr;
+  unsigned long long ctx_id = 0;  // the context the address belongs to
+};
+Cached g_scratch[kMaxDevices];
+
+// Context identity through the driver API, reached via the runtime's entry-point query
+// (no link against libcuda): a device reset (cudaDeviceReset) destroys the context that
+// holds the array, and a later call must look the address up again in the new one.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) ==
+            cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
+            cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess) {
+      get_current = (CtxGetCurrentFn)f1;
+      get_id = (CtxGetIdFn)f2;
+    }
+    cudaGetLastError();
+  }
+  if (!get_current || !get_id) return false;
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 // Device address of g_cheb_scratch on the current device. In host code the symbol
-// name is only a host-side stand-in, so the address is looked up once per device,
-// with that device current, and cached.
+// name is only a host-side stand-in, so the address is looked up with the device
+// current, once per device and context, and cached. Under lazy module loading the
+// lookup is also what loads the module and so materialises the array on the device.
 int scratch_address(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return IPM_ECUDA;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_addr[dev]) {
+  unsigned long long id = 0;
+  bool known = current_context_id(&id);
+  Cached& c = g_scratch[dev];
+  if (!c.addr || !known || c.ctx_id != id) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_cheb_scratch) != cudaSuccess) {
       cudaGetLastError();
+      c.addr = nullptr;
       return IPM_ECUDA;
     }
-    g_scratch_addr[dev] = (double*)p;
+    c.addr = (double*)p;
+    c.ctx_id = current_context_id(&id) ? id : 0;
   }
-  *out = g_scratch_addr[dev];
+  *out = c.addr;
   return IPM_OK;
 }
 

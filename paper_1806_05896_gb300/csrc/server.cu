@@ -80,23 +80,27 @@ struct ipm_server {
   std::map<ipm_solver*, size_t> owned;  // every solver with its bytes
   std::vector<std::thread> workers;
 
-  // evict one idle solver (any grid); caller holds the lock
-  bool evict_one() {
+  // take one idle solver (any grid) out of the pool into `dead`; the caller holds the lock
+  // and destroys `dead` after releasing it (ipm_destroy frees device memory, which can
+  // synchronise the device, and must not block the other workers)
+  bool evict_one(std::vector<ipm_solver*>& dead) {
     for (auto& kv : idle) {
       if (kv.second.empty()) continue;
       ipm_solver* s = kv.second.back();
       kv.second.pop_back();
       used -= owned[s];
       owned.erase(s);
-      ipm_destroy(s);
+      dead.push_back(s);
       return true;
     }
     return false;
   }
 
   // first admissible request: a pooled solver is free, or its memory fits the budget
-  // (evicting idle solvers of other grids when that makes room); caller holds the lock
-  Request* admit(ipm_solver** reuse) {
+  // (evicting idle solvers of other grids when that makes room); caller holds the lock.
+  // The budget is soft for pooled solvers: a reused solver's Krylov basis can grow during
+  // its solve, and the growth is accounted when the solve ends.
+  Request* admit(ipm_solver** reuse, std::vector<ipm_solver*>& dead) {
     for (auto it = queue.begin(); it != queue.end(); ++it) {
       Request* r = *it;
       auto pit = idle.find(key_of(r->rq));
@@ -106,7 +110,7 @@ struct ipm_server {
         queue.erase(it);
         return r;
       }
-      while (used + r->need > budget && evict_one()) {
+      while (used + r->need > budget && evict_one(dead)) {
       }
       if (used + r->need <= budget) {
         used += r->need;
@@ -125,10 +129,15 @@ struct ipm_server {
     while (true) {
       Request* r = nullptr;
       ipm_solver* s = nullptr;
+      std::vector<ipm_solver*> dead;
       {
         std::unique_lock<std::mutex> lk(mu);
-        cv_work.wait(lk, [&] { return stop || (r = admit(&s)) != nullptr; });
-        if (!r) break;
+        cv_work.wait(lk, [&] { return stop || (r = admit(&s, dead)) != nullptr || !dead.empty(); });
+      }
+      for (ipm_solver* d : dead) ipm_destroy(d);  // outside the lock, before any new solver
+      if (!r) {
+        if (!dead.empty()) continue;  // evictions made room for nothing yet: look again
+        break;
       }
       r->t_start = Clock::now();
       int rc = IPM_OK;
@@ -230,7 +239,9 @@ int ipm_server_wait(ipm_server* sv, long long ticket, ipm_report* rep, double* u
   lk.unlock();
   int rc = r->status;
   if (rep) *rep = r->rep;
-  if (u && rc != IPM_EINVAL) {
+  // a control exists only for a solve that ran (converged or not); any other status is
+  // returned unchanged, without touching u
+  if (u && (rc == IPM_OK || rc == IPM_ENOTCONV)) {
     if (len != r->u.size()) rc = IPM_EINVAL;
     else std::memcpy(u, r->u.data(), len * sizeof(double));
   }

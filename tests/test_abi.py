@@ -59,3 +59,27 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "from oracle" not in src and "import oracle" not in src
+
+
+def test_server_wait_returns_the_solves_own_error(lib):
+    """A request whose solver cannot be created reports the creation's status through
+    ipm_server_wait, not an argument error about the control buffer. Without a GPU the
+    creation fails with IPM_ENOMEM / IPM_ECUDA; with one, bounds violating u_a < 0 < u_b
+    make it fail with IPM_EINVAL. Either way the returned code is the creation's."""
+    import numpy as np
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    sv = ipm.Server(workers=1, budget_bytes=1 << 30)
+    try:
+        n = 9
+        ub = 1.0 if not has_gpu else -1.0
+        t = sv.submit(2, n, 1e-2, 1e-3, -1.0, ub, np.zeros(n * n))
+        with pytest.raises(ipm.IpmError) as e:
+            sv.wait(t)
+        want = (ipm.EINVAL,) if has_gpu else (ipm.ENOMEM, ipm.ECUDA)
+        assert e.value.code in want
+    finally:
+        sv.close()
