@@ -54,6 +54,7 @@ struct ipm_solver {
   cudaStream_t stream = nullptr;
   cudaStream_t own = nullptr;
   std::vector<void*> allocs;
+  std::vector<size_t> alloc_bytes;  // size of each entry of allocs
   size_t bytes = 0;
 
   IpmState st{};
@@ -138,6 +139,7 @@ struct ipm_solver {
     }
     CK(cudaMemset(p, 0, b));
     allocs.push_back(p);
+    alloc_bytes.push_back(b);
     bytes += b;
     return (T*)p;
   }
@@ -218,6 +220,7 @@ struct ipm_solver {
     prof_ev.clear();
     for (void* p : allocs) cudaFree(p);
     allocs.clear();
+    alloc_bytes.clear();
     if (hbuf) cudaFreeHost(hbuf);
     hbuf = nullptr;
     if (own) cudaStreamDestroy(own);
@@ -1152,6 +1155,23 @@ struct ipm_solver {
     hist.insert(hist.end(), row, row + kHistCols);
   }
 
+  // After a breakdown, a non-finite scalar (a norm, a step length) may have been applied to
+  // whole arrays, so boundary and padding entries, which kernels read as zero but never
+  // write, can hold NaN. Zero every work array; the problem data (bounds, data vectors,
+  // Dirichlet lift, operator coefficients) are kept.
+  void scrub_work() {
+    std::vector<const void*> keep = {ya, yb, zbw, zbv, cy, fvec, glift, ydbuf, fbuf};
+    for (const OpL& op : lvop) {
+      keep.push_back(op.coef);
+      keep.push_back(op.coef32);
+    }
+    for (size_t i = 0; i < allocs.size(); ++i) {
+      if (std::find(keep.begin(), keep.end(), allocs[i]) != keep.end()) continue;
+      CK(cudaMemsetAsync(allocs[i], 0, alloc_bytes[i], stream));
+    }
+    sync();
+  }
+
   void apply_flags(const ipm_options& o) {
     fused = (o.kernel_flags & 1) == 0;
     ff_outer = (o.kernel_flags & 16) == 0;
@@ -1349,7 +1369,16 @@ int ipm_solve(ipm_solver* s, const ipm_options* opt, ipm_report* rep) {
   ipm_options o;
   if (opt) o = *opt;
   else ipm_default_options(&o);
-  return guarded(s, [&] { return s->solve(o, rep); });
+  int rc = guarded(s, [&] { return s->solve(o, rep); });
+  if (rc == IPM_EBREAKDOWN) {
+    // leave the solver usable for new data: clear what the non-finite values touched
+    int rs = guarded(s, [&] {
+      s->scrub_work();
+      return IPM_OK;
+    });
+    if (rs != IPM_OK) return rs;
+  }
+  return rc;
 }
 
 static int get_common(const ipm_solver* s, int which, double* out, size_t len, bool dev) {
