@@ -83,7 +83,8 @@ enum { IPM_STOP_PAPER = 0, IPM_STOP_KKT = 1, IPM_STOP_FIXED = 2 };
  * steps, 3 V-cycles with 5 pre- and 5 post-smoothing steps.
  *   precision: IPM_PREC_FP64 everywhere, or IPM_PREC_MIXED (Chebyshev and
  *              multigrid in FP32; Krylov recurrences, operator and IPM in FP64;
- *              the Krylov method is then flexible GMRES).
+ *              GMRES is then flexible GMRES, and MINRES runs inside an FP64
+ *              iterative refinement loop that restores krylov_tol on the true residual).
  *   krylov:    IPM_KRYLOV_MINRES_PD (MINRES + P_D) or IPM_KRYLOV_GMRES_PT
  *              (GMRES + P_T, right-preconditioned, flexible form).
  *   stop:      IPM_STOP_PAPER: ||xi_p|| <= eps_p, ||xi_d|| <= eps_d, ||xi_c|| <= eps_c
@@ -111,7 +112,12 @@ typedef struct {
                        outer residual in FP64 instead of float-float arithmetic;
                        bit 5: mixed FGMRES keeps its Arnoldi basis in FP64 instead of
                        float-float (orthogonalisation and norms); bit 6: with a float-float
-                       basis, apply P_T to its FP64 conversion instead of in float-float */
+                       basis, apply P_T to its FP64 conversion instead of in float-float;
+                       bit 7: run the FP32 multigrid levels from 129^2 down as one persistent
+                       cooperative launch per V-cycle instead of one launch per level (same
+                       results to FP32 accuracy; fewer launches, no faster on GB300);
+                       bit 8: mixed-precision MINRES without its FP64 iterative refinement;
+                       bit 9: no tile-shape autotuning (the fixed shapes of a timing sweep) */
 } ipm_options;
 
 typedef struct {
@@ -182,6 +188,20 @@ long long ipm_launch_count(void);
  * jinv read, x written), in the precision of the last solve. */
 int ipm_profile_smoother(ipm_solver* s, int enable, int every);
 int ipm_profile_read(ipm_solver* s, double* total_ms, long long* launches, double* bytes_per_launch);
+/* The same sampling for one of several kernels of the 2D fused multigrid path and the
+ * Krylov iteration: kind 0 the finest-level pre-smoothing + restriction, 1 the finest-level
+ * prolongation + post-smoothing, 2 the one-CTA coarse cycle (or, with kernel_flags bit 7,
+ * the persistent cycle from 129^2 down), 3 the saddle operator of (NewtonSystem), 4 the
+ * tiled launches of the levels between the finest and the coarse cycle.
+ * ipm_profile_kernel_read returns the summed event time of the sampled launches, their
+ * number, the number of launches of that kind since enabling (sampled or not), and the
+ * average algorithmic bytes of a sampled launch counted two ways: bytes_pass, every sweep
+ * or pass reading its operands and writing its result once (the per-pass count of a
+ * stencil sweep); bytes_once, every value a launch needs read or written once (what a
+ * temporally blocked kernel moves at best). */
+int ipm_profile_kernel(ipm_solver* s, int kind, int enable, int every);
+int ipm_profile_kernel_read(ipm_solver* s, double* total_ms, long long* sampled, long long* calls,
+                            double* bytes_pass, double* bytes_once);
 /* Per-stage CUDA-event timing of the Krylov iteration (disables graph replay while on).
  * Copies the accumulated milliseconds and counts of up to `nphases` stages into ms /
  * counts (stages: 1 Chebyshev, 2 z-block + coupling, 3 multigrid solves, 4 (M + Theta_y)
@@ -191,6 +211,17 @@ int ipm_profile_read(ipm_solver* s, double* total_ms, long long* launches, doubl
  * 12 the one-CTA coarse cycle), then, if enable >= 0, resets them and switches
  * stage timing on (1) or off (0). */
 int ipm_profile_phases(ipm_solver* s, int enable, double* ms, long long* counts, int nphases);
+/* Tile shapes chosen so far by the autotuner of the FP32 multigrid kernels (the first
+ * mixed-precision solve on a grid size times every candidate shape once per process and
+ * device; shapes change timing only, not results): text lines "kernel n=.. dev=..: shape
+ * time" into buf (len bytes, NUL-terminated, may be NULL); returns the full text length. */
+int ipm_tuning_report(char* buf, size_t len);
+/* Pin the tile shape of kernel 0 (pre-smoothing + restriction) or 1 (prolongation +
+ * post-smoothing) for grid size n on the current device (shape = index into the
+ * candidates: pre 52x52/16w, 20x32/8w, 52x32/8w, 52x24/8w, 20x64/8w; post 56x32/8w,
+ * 24x24/8w, 56x56/16w, 24x48/8w, 56x24/8w), or forget it (shape < 0) so that the next solve
+ * tunes again. For reproducible kernel selection. IPM_EINVAL for an unknown kernel/shape. */
+int ipm_tuning_set(int kernel, int n, int shape);
 const char* ipm_strerror(int code);
 const char* ipm_last_error(const ipm_solver* s);
 

@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import time
 from typing import Callable, List, Optional
 
 import numpy as np
@@ -190,6 +191,8 @@ def _symmetric(A: sp.csr_matrix) -> bool:
 class KrylovStats:
     iterations: int
     relres: float
+    setup_s: float = 0.0    # preconditioner construction (multigrid hierarchy or LU)
+    solve_s: float = 0.0    # the FGMRES iterations
 
 
 def fgmres(A: sp.spmatrix, b: np.ndarray, prec: Callable[[np.ndarray], np.ndarray],
@@ -258,16 +261,21 @@ def fgmres(A: sp.spmatrix, b: np.ndarray, prec: Callable[[np.ndarray], np.ndarra
 
 
 def newton_solver(inner: str = "gmg", tol: float = 1e-12, restart: int = 40,
-                  vcycles: int = 2, stats: Optional[list] = None, accept: float = 1e-10):
+                  vcycles: int = 2, stats: Optional[list] = None, accept: float = 1e-10,
+                  maxiter: int = 2000):
     """A Newton-system solver for ``oracle.ipm.solve``: FGMRES + P_T to true relative
     residual ``tol``, or until a restart cycle no longer halves it (the FP64 attainable
     accuracy, which for strongly scaled late barrier systems lies near 1e-12); a final
-    true relative residual above ``accept`` raises. Appends a :class:`KrylovStats` per
-    solve to ``stats`` if given."""
+    true relative residual above ``accept`` raises (``maxiter`` caps the iterations, for
+    timing samples). Appends a :class:`KrylovStats` per solve to ``stats`` if given."""
 
     def solve(qp: QP, A: sp.spmatrix, b: np.ndarray, th_y, th_w, th_v) -> np.ndarray:
+        t0 = time.perf_counter()
         P = BlockTriangular(qp, th_y, th_w, th_v, inner=inner, vcycles=vcycles)
-        x, st = fgmres(A.tocsr(), b, P, tol=tol, restart=restart)
+        t1 = time.perf_counter()
+        x, st = fgmres(A.tocsr(), b, P, tol=tol, restart=restart, maxiter=maxiter)
+        st.setup_s = t1 - t0
+        st.solve_s = time.perf_counter() - t1
         if not st.relres <= accept:
             raise RuntimeError(f"FGMRES did not reach {accept:g}: {st.relres:.3e} "
                                f"after {st.iterations} iterations")

@@ -15,6 +15,9 @@
 //
 // A V-cycle on a 1025^2 grid thus takes 2 launches per level above the coarse
 // block plus one, instead of about 14 per level.
+#include <cstdio>
+#include <string>
+#include <tuple>
 #include <map>
 #include <mutex>
 #include <type_traits>
@@ -326,21 +329,18 @@ IPM_D void rb_pass(const float* __restrict__ cur, float* __restrict__ nxt,
   }
 }
 
+// pre-smoothing (NU sweeps from xin, or from zero), residual and full-weighting restriction
+// of the tile with first interior node (X0, Y0); smem holds the two tile buffers
 template <int TX, int TY, int NU, int NW>
-__global__ void __launch_bounds__(NW * 32) k_mg2_pre_restrict_rb(GridDesc g, GridDesc gc,
-                                                                 const float* __restrict__ xin,
-                                                                 float* __restrict__ xout,
-                                                                 const float* __restrict__ b,
-                                                                 const float* __restrict__ m,
-                                                                 float* __restrict__ bc,
-                                                                 float omega, int zero_init) {
+IPM_D void pre_restrict_rb_tile(const GridDesc& g, const GridDesc& gc, const float* __restrict__ xin,
+                                float* __restrict__ xout, const float* __restrict__ b,
+                                const float* __restrict__ m, float* __restrict__ bc, float omega,
+                                int zero_init, int X0, int Y0, unsigned char* smem_raw) {
   constexpr int H = NU + 2;
   using S = RBShape<TX, TY, H, NW>;
   constexpr int SX = S::SX;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   float* cur = reinterpret_cast<float*>(smem_raw);
   float* nxt = cur + SX * S::SY;
-  const int X0 = 1 + blockIdx.x * TX, Y0 = 1 + blockIdx.y * TY;
   const long long p = g.pitch;
   float rb[S::CX][S::K], rm[S::CX][S::K], rj[S::CX][S::K];
   auto load_x = [&](int gx, int gy) { return zero_init ? 0.f : xin[(long long)gy * p + gx]; };
@@ -370,19 +370,29 @@ __global__ void __launch_bounds__(NW * 32) k_mg2_pre_restrict_rb(GridDesc g, Gri
 }
 
 template <int TX, int TY, int NU, int NW>
-__global__ void __launch_bounds__(NW * 32) k_mg2_prolong_post_rb(GridDesc g, GridDesc gc,
+__global__ void __launch_bounds__(NW * 32) k_mg2_pre_restrict_rb(GridDesc g, GridDesc gc,
                                                                  const float* __restrict__ xin,
-                                                                 const float* __restrict__ xc,
                                                                  float* __restrict__ xout,
                                                                  const float* __restrict__ b,
                                                                  const float* __restrict__ m,
-                                                                 float omega) {
+                                                                 float* __restrict__ bc,
+                                                                 float omega, int zero_init) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pre_restrict_rb_tile<TX, TY, NU, NW>(g, gc, xin, xout, b, m, bc, omega, zero_init,
+                                       1 + blockIdx.x * TX, 1 + blockIdx.y * TY, smem_raw);
+}
+
+// prolongation of the coarse correction xc onto xin and NU post-smoothing sweeps of the tile
+// with first interior node (X0, Y0) into xout
+template <int TX, int TY, int NU, int NW>
+IPM_D void prolong_post_rb_tile(const GridDesc& g, const GridDesc& gc, const float* __restrict__ xin,
+                                const float* __restrict__ xc, float* __restrict__ xout,
+                                const float* __restrict__ b, const float* __restrict__ m,
+                                float omega, int X0, int Y0, unsigned char* smem_raw) {
   constexpr int H = NU;
   using S = RBShape<TX, TY, H, NW>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   float* cur = reinterpret_cast<float*>(smem_raw);
   float* nxt = cur + S::SX * S::SY;
-  const int X0 = 1 + blockIdx.x * TX, Y0 = 1 + blockIdx.y * TY;
   const long long p = g.pitch;
   const int cp = gc.pitch;
   float rb[S::CX][S::K], rm[S::CX][S::K], rj[S::CX][S::K];
@@ -402,32 +412,112 @@ __global__ void __launch_bounds__(NW * 32) k_mg2_prolong_post_rb(GridDesc g, Gri
   rb_pass<kRBSweepOut, TX, TY, H, NW>(cur, nxt, rb, rm, rj, xout, g, X0, Y0);
 }
 
+template <int TX, int TY, int NU, int NW>
+__global__ void __launch_bounds__(NW * 32) k_mg2_prolong_post_rb(GridDesc g, GridDesc gc,
+                                                                 const float* __restrict__ xin,
+                                                                 const float* __restrict__ xc,
+                                                                 float* __restrict__ xout,
+                                                                 const float* __restrict__ b,
+                                                                 const float* __restrict__ m,
+                                                                 float omega) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  prolong_post_rb_tile<TX, TY, NU, NW>(g, gc, xin, xc, xout, b, m, omega, 1 + blockIdx.x * TX,
+                                       1 + blockIdx.y * TY, smem_raw);
+}
+
 // ---------------------------------------------------------------------------
 // One CTA, all coarse levels in shared memory (dense n x n per level).
 // ---------------------------------------------------------------------------
-// one damped-Jacobi sweep over the interior of an n x n level (threads as 32 x 32 grid)
-template <typename T>
-IPM_D void cta_sweep(const T* cur, T* nxt, const T* sb, const T* sm, const T* sj, int n, int zero) {
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
-  for (int iy = 1 + ty; iy < n - 1; iy += ny)
-    for (int ix = 1 + tx; ix < n - 1; ix += 32) {
-      const int i = iy * n + ix;
-      T xc = zero ? T(0) : cur[i];
-      T ax = zero ? T(0) : apply_A(cur, i, n, sm[i]);
-      nxt[i] = xc + sj[i] * (sb[i] - ax);
-    }
+// Work split of one level: the m = n - 2 interior columns times R row groups of K
+// consecutive rows; thread t < m R owns column c = t % m, rows 1 + g K ... of group g = t / m.
+// A thread reads its column and the two beside it once per row of its window (K + 2 rows)
+// and forms the horizontal triple sums once, which the K outputs share.
+constexpr int kCoarseK = 4;        // rows per thread at most (65^2: 63 columns x 16 groups of 4)
+constexpr int kCoarseSmallN = 17;  // levels up to 17^2 run on the first 8 warps only
+constexpr int kCoarseSmallThreads = 256;
+
+struct Strip {
+  int c, iy0, K;
+  bool active;
+};
+
+IPM_D Strip strip_of(int n, int nthreads) {
+  const int m = n - 2;
+  int R = nthreads / m;
+  if (R > m) R = m;
+  if (R < 1) R = 1;
+  Strip s;
+  s.K = (m + R - 1) / R;
+  const int t = threadIdx.x;
+  s.active = t < m * R;
+  s.c = t % m;
+  s.iy0 = 1 + (t / m) * s.K;
+  return s;
 }
 
+// mode 0: one damped-Jacobi sweep into out; mode 1: residual b - A x into out.
+// zero: the iterate is zero (first sweep from x = 0).
 template <typename T>
-__global__ void __launch_bounds__(1024) k_mg2_coarse(MGCoarse<T> cl, const T* __restrict__ btop,
-                                                     T* __restrict__ xtop, T omega, int nu_pre,
-                                                     int nu_post, int load_x) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+IPM_D void strip_pass(const T* __restrict__ cur, T* __restrict__ out, const T* __restrict__ sb,
+                      const T* __restrict__ sm, const T* __restrict__ sj, int n, const Strip& st,
+                      int mode, bool zero) {
+  if (!st.active) return;
+  const int ix = st.c + 1;
+  if (zero) {
+#pragma unroll
+    for (int k = 0; k < kCoarseK; ++k) {
+      const int iy = st.iy0 + k;
+      if (k < st.K && iy <= n - 2) {
+        const int i = iy * n + ix;
+        out[i] = mode == 0 ? T(0) + sj[i] * (sb[i] - T(0)) : sb[i];
+      }
+    }
+    return;
+  }
+  T h[kCoarseK + 2], xm[kCoarseK + 2];
+#pragma unroll
+  for (int k = 0; k < kCoarseK + 2; ++k) {
+    const int iy = st.iy0 - 1 + k;
+    h[k] = T(0);
+    xm[k] = T(0);
+    if (k < st.K + 2 && iy <= n - 1) {
+      const T* r = cur + iy * n + ix;
+      xm[k] = r[0];
+      h[k] = (r[-1] + r[0]) + r[1];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kCoarseK; ++k) {
+    const int iy = st.iy0 + k;
+    if (k < st.K && iy <= n - 2) {
+      const int i = iy * n + ix;
+      const T xc = xm[k + 1];
+      const T box = (h[k] + h[k + 1]) + h[k + 2];
+      const T ax = (T(3) * xc - box * T(1.0 / 3.0)) + sm[i] * xc;
+      out[i] = mode == 0 ? xc + sj[i] * (sb[i] - ax) : sb[i] - ax;
+    }
+  }
+}
+
+// synchronisation of the threads working on a level: the whole CTA, or the first
+// kCoarseSmallThreads threads (named barrier 1) on the small levels
+IPM_D void coarse_sync(bool small) {
+  if (small) asm volatile("bar.sync 1, %0;" ::"n"(kCoarseSmallThreads) : "memory");
+  else __syncthreads();
+}
+
+// the V-cycle on the levels of cl, run by the whole CTA (any block size that is a multiple
+// of 32, at least kCoarseSmallThreads, with no level above 65^2 for 1024 threads or above
+// 33^2 for 256 threads); smem_raw holds mg2_coarse_smem(cl) bytes
+template <typename T>
+IPM_D void coarse_cycle(const MGCoarse<T>& cl, const T* __restrict__ btop, T* __restrict__ xtop,
+                        T omega, int nu_pre, int nu_post, int load_x, unsigned char* smem_raw) {
   T* base = reinterpret_cast<T*>(smem_raw);
   // per-level size and offset of the six arrays (x0, x1, b, r, m, jinv) in a shared table,
   // and the current-iterate parity of every level as a register bit mask: indexing
   // per-thread arrays by the runtime level index would put them in local memory
   __shared__ int s_n[kMaxCoarse], s_off[kMaxCoarse];
+  __shared__ unsigned s_cur;
   if (threadIdx.x == 0) {
     int off = 0;
     for (int l = 0; l < cl.nl; ++l) {
@@ -443,13 +533,14 @@ __global__ void __launch_bounds__(1024) k_mg2_coarse(MGCoarse<T> cl, const T* __
   // zero everything, then load b (top level) and m (all levels), interior entries
   for (int t = threadIdx.x; t < total; t += blockDim.x) base[t] = T(0);
   __syncthreads();
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int l = 0; l < cl.nl; ++l) {
     const int n = s_n[l];
     T* Ml = arr(l, AM);
     T* Jl = arr(l, AJ);
     const T* mg = cl.m[l];
     const long long pl = cl.pitch[l];
+    const int ny = blockDim.x >> 5;
     for (int iy = 1 + ty; iy < n - 1; iy += ny)
       for (int ix = 1 + tx; ix < n - 1; ix += 32) {
         T mm = mg[(long long)iy * pl + ix];
@@ -464,73 +555,180 @@ __global__ void __launch_bounds__(1024) k_mg2_coarse(MGCoarse<T> cl, const T* __
   auto xcur = [&](int l) { return arr(l, ((cur >> l) & 1u) ? AX1 : AX0); };
   auto xnxt = [&](int l) { return arr(l, ((cur >> l) & 1u) ? AX0 : AX1); };
   const int L = cl.nl - 1;
-  for (int l = 0; l < L; ++l) {
+  int ls = 0;  // first small level
+  while (ls < L && s_n[ls] > kCoarseSmallN) ++ls;
+
+  // pre-smoothing, residual and full-weighting restriction of level l
+  auto descend = [&](int l, bool small) {
     const int n = s_n[l];
+    const int nthr = small ? kCoarseSmallThreads : (int)blockDim.x;
+    const Strip st = strip_of(n, nthr);
     const T* Bl = arr(l, AB);
     const T* Ml = arr(l, AM);
     const T* Jl = arr(l, AJ);
     T* Rl = arr(l, AR);
     for (int s = 0; s < nu_pre; ++s) {
-      cta_sweep(xcur(l), xnxt(l), Bl, Ml, Jl, n, s == 0 && !(l == 0 && load_x));
+      strip_pass(xcur(l), xnxt(l), Bl, Ml, Jl, n, st, 0, s == 0 && !(l == 0 && load_x));
       cur ^= 1u << l;
-      __syncthreads();
+      coarse_sync(small);
     }
-    {
-      const T* c = xcur(l);
-      for (int iy = 1 + ty; iy < n - 1; iy += ny)
-        for (int ix = 1 + tx; ix < n - 1; ix += 32) {
-          const int i = iy * n + ix;
-          Rl[i] = Bl[i] - apply_A(c, i, n, Ml[i]);
-        }
-    }
-    __syncthreads();
-    {
-      const int nc = s_n[l + 1];
-      T* Bc = arr(l + 1, AB);
-      for (int J = 1 + ty; J < nc - 1; J += ny)
-        for (int I = 1 + tx; I < nc - 1; I += 32) {
-          const int i = (2 * J) * n + 2 * I;
-          const T* r = Rl;
-          T r0 = T(0.5) * r[i - n - 1] + r[i - n] + T(0.5) * r[i - n + 1];
-          T r1 = T(0.5) * r[i - 1] + r[i] + T(0.5) * r[i + 1];
-          T r2 = T(0.5) * r[i + n - 1] + r[i + n] + T(0.5) * r[i + n + 1];
-          Bc[J * nc + I] = T(0.5) * r0 + r1 + T(0.5) * r2;
-        }
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {  // coarsest grid: 3 nodes per direction, one unknown
-    const int i = 1 * 3 + 1;
-    arr(L, AX0)[i] = arr(L, AB)[i] / (T(8.0 / 3.0) + arr(L, AM)[i]);
-  }
-  cur &= ~(1u << L);
-  __syncthreads();
-  for (int l = L - 1; l >= 0; --l) {
+    strip_pass(xcur(l), Rl, Bl, Ml, Jl, n, st, 1, false);
+    coarse_sync(small);
+    const int nc = s_n[l + 1];
+    T* Bc = arr(l + 1, AB);
+    const int ny = nthr >> 5;
+    for (int J = 1 + ty; J < nc - 1; J += ny)
+      for (int I = 1 + tx; I < nc - 1; I += 32) {
+        const int i = (2 * J) * n + 2 * I;
+        const T* r = Rl;
+        T r0 = T(0.5) * r[i - n - 1] + r[i - n] + T(0.5) * r[i - n + 1];
+        T r1 = T(0.5) * r[i - 1] + r[i] + T(0.5) * r[i + 1];
+        T r2 = T(0.5) * r[i + n - 1] + r[i + n] + T(0.5) * r[i + n + 1];
+        Bc[J * nc + I] = T(0.5) * r0 + r1 + T(0.5) * r2;
+      }
+    coarse_sync(small);
+  };
+  // prolongation of the coarse correction and post-smoothing of level l
+  auto ascend = [&](int l, bool small) {
     const int n = s_n[l], nc = s_n[l + 1];
+    const int nthr = small ? kCoarseSmallThreads : (int)blockDim.x;
+    const Strip st = strip_of(n, nthr);
     T* c = xcur(l);
     const T* xcs = xcur(l + 1);
     const bool wipe = nu_pre == 0 && !(l == 0 && load_x);  // x never written on this level
-    for (int iy = 1 + ty; iy < n - 1; iy += ny)
-      for (int ix = 1 + tx; ix < n - 1; ix += 32) {
-        T base_v = wipe ? T(0) : c[iy * n + ix];
-        c[iy * n + ix] = base_v + prolong_at(xcs, nc, ix, iy);
+    if (st.active) {
+      const int ix = st.c + 1;
+#pragma unroll
+      for (int k = 0; k < kCoarseK; ++k) {
+        const int iy = st.iy0 + k;
+        if (k < st.K && iy <= n - 2) {
+          T base_v = wipe ? T(0) : c[iy * n + ix];
+          c[iy * n + ix] = base_v + prolong_at(xcs, nc, ix, iy);
+        }
       }
-    __syncthreads();
+    }
+    coarse_sync(small);
     const T* Bl = arr(l, AB);
     const T* Ml = arr(l, AM);
     const T* Jl = arr(l, AJ);
     for (int s = 0; s < nu_post; ++s) {
-      cta_sweep(xcur(l), xnxt(l), Bl, Ml, Jl, n, 0);
+      strip_pass(xcur(l), xnxt(l), Bl, Ml, Jl, n, st, 0, false);
       cur ^= 1u << l;
-      __syncthreads();
+      coarse_sync(small);
     }
+  };
+
+  for (int l = 0; l < ls; ++l) descend(l, false);
+  if (threadIdx.x < kCoarseSmallThreads) {
+    for (int l = ls; l < L; ++l) descend(l, true);
+    if (threadIdx.x == 0) {  // coarsest grid: 3 nodes per direction, one unknown
+      const int i = 1 * 3 + 1;
+      arr(L, AX0)[i] = arr(L, AB)[i] / (T(8.0 / 3.0) + arr(L, AM)[i]);
+    }
+    cur &= ~(1u << L);
+    coarse_sync(true);
+    for (int l = L - 1; l >= ls; --l) ascend(l, true);
+    if (threadIdx.x == 0) s_cur = cur;
   }
+  __syncthreads();
+  cur = s_cur;  // the small levels' parities, set by the threads that ran them
+  for (int l = ls - 1; l >= 0; --l) ascend(l, false);
   {
     const int n = s_n[0];
     const T* c = xcur(0);
+    const int ny = blockDim.x >> 5;
     for (int iy = 1 + ty; iy < n - 1; iy += ny)
       for (int ix = 1 + tx; ix < n - 1; ix += 32) xtop[(long long)iy * cl.pitch[0] + ix] = c[iy * n + ix];
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_mg2_coarse(MGCoarse<T> cl, const T* __restrict__ btop,
+                                                     T* __restrict__ xtop, T omega, int nu_pre,
+                                                     int nu_post, int load_x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  coarse_cycle<T>(cl, btop, xtop, omega, nu_pre, nu_post, load_x, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent V-cycle below the finest level (cooperative launch, grid-wide barriers).
+// ---------------------------------------------------------------------------
+constexpr int kMidPreTX = 20, kMidPreTY = 32, kMidPostT = 24, kMidNW = 8;
+constexpr long long kBarrierSpins = 1ll << 22;  // a few seconds at most with the sleeps
+
+// All blocks of the grid meet here (the blocks are co-resident: cooperative launch).
+// Thread 0 of each block arrives on a counter; the last one resets it and advances the
+// generation, the others wait for the generation to change. A wait beyond the spin budget
+// sets bar->timeout and returns false (as does any wait once a timeout is recorded).
+IPM_D bool grid_barrier(GridBarrier* bar, unsigned nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &bar->gen;
+    volatile int* vto = &bar->timeout;
+    const unsigned g0 = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == g0) {
+        if (*vto || ++spins > kBarrierSpins) {
+          atomicExch(&bar->timeout, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kMidNW * 32) k_mg2_mid_cycle(MidCycle mc, GridBarrier* bar,
+                                                               float omega) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const unsigned nb = gridDim.x;
+  bool ok = true;
+  for (int l = 0; l < mc.nt && ok; ++l) {
+    const GridDesc& g = mc.g[l];
+    const int tx = (g.n - 2 + kMidPreTX - 1) / kMidPreTX, ty = (g.n - 2 + kMidPreTY - 1) / kMidPreTY;
+    for (int t = blockIdx.x; t < tx * ty; t += gridDim.x) {
+      __syncthreads();  // the block's previous tile is done with the shared buffers
+      pre_restrict_rb_tile<kMidPreTX, kMidPreTY, kRBSweeps, kMidNW>(
+          g, mc.g[l + 1], nullptr, mc.xb[l], mc.b[l], mc.m[l], mc.bnext[l], omega, 1,
+          1 + (t % tx) * kMidPreTX, 1 + (t / tx) * kMidPreTY, smem_raw);
+    }
+    ok = grid_barrier(bar, nb);
+  }
+  if (ok) {
+    if (blockIdx.x == 0)
+      coarse_cycle<float>(mc.cl, mc.bnext[mc.nt - 1], mc.xcoarse, omega, kRBSweeps, kRBSweeps, 0,
+                          smem_raw);
+    ok = grid_barrier(bar, nb);
+  }
+  for (int l = mc.nt - 1; l >= 0 && ok; --l) {
+    const GridDesc& g = mc.g[l];
+    const float* xc = l == mc.nt - 1 ? mc.xcoarse : mc.xa[l + 1];
+    const int tx = (g.n - 2 + kMidPostT - 1) / kMidPostT;
+    for (int t = blockIdx.x; t < tx * tx; t += gridDim.x) {
+      __syncthreads();
+      prolong_post_rb_tile<kMidPostT, kMidPostT, kRBSweeps, kMidNW>(
+          g, mc.g[l + 1], mc.xb[l], xc, mc.xa[l], mc.b[l], mc.m[l], omega,
+          1 + (t % tx) * kMidPostT, 1 + (t / tx) * kMidPostT, smem_raw);
+    }
+    ok = grid_barrier(bar, nb);
+  }
+  // a barrier that gave up leaves a non-finite value in the cycle's output, which the
+  // Krylov iteration reports as a breakdown
+  if (blockIdx.x == 0 && threadIdx.x == 0 && *(volatile int*)&bar->timeout)
+    mc.xa[0][mc.g[0].pitch + 1] = __int_as_float(0x7fc00000);
 }
 
 template <typename T>
@@ -605,16 +803,70 @@ void prolong_post_rb(const GridDesc& g, const GridDesc& gc, const float* xin, co
                                                                  (float)omega);
 }
 
+// ---------------------------------------------------------------------------
+// Tile-shape autotuning of the register-blocked FP32 kernels. Candidate shapes keep the
+// halo'd tile width a whole number of 32-lane column groups (TX + 12 for the 7-node halo
+// of pre-smoothing, TX + 8 for the 5-node halo of post-smoothing); every shape computes
+// each node with the same arithmetic, so the choice changes timing only. The choice per
+// (kernel, grid size, device) is made once per process by timing every candidate on the
+// caller's buffers (mg2_autotune); until then, and for sizes never tuned, the fixed rule
+// of the timing sweep that chose the defaults applies.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kPreShapes = 5, kPostShapes = 5;
+const char* const kPreShapeNames[kPreShapes] = {"52x52/16w", "20x32/8w", "52x32/8w", "52x24/8w",
+                                                "20x64/8w"};
+const char* const kPostShapeNames[kPostShapes] = {"56x32/8w", "24x24/8w", "56x56/16w", "24x48/8w",
+                                                  "56x24/8w"};
+
+void pre_rb_shape(int c, const GridDesc& g, const GridDesc& gc, const float* xin, float* xout,
+                  const float* b, const float* m, float* bc, double omega, int zero_init,
+                  cudaStream_t s) {
+  switch (c) {
+    case 0: pre_restrict_rb<52, 52, 16>(g, gc, xin, xout, b, m, bc, omega, zero_init, s); break;
+    case 1: pre_restrict_rb<20, 32, 8>(g, gc, xin, xout, b, m, bc, omega, zero_init, s); break;
+    case 2: pre_restrict_rb<52, 32, 8>(g, gc, xin, xout, b, m, bc, omega, zero_init, s); break;
+    case 3: pre_restrict_rb<52, 24, 8>(g, gc, xin, xout, b, m, bc, omega, zero_init, s); break;
+    default: pre_restrict_rb<20, 64, 8>(g, gc, xin, xout, b, m, bc, omega, zero_init, s); break;
+  }
+}
+
+void post_rb_shape(int c, const GridDesc& g, const GridDesc& gc, const float* xin, const float* xc,
+                   float* xout, const float* b, const float* m, double omega, cudaStream_t s) {
+  switch (c) {
+    case 0: prolong_post_rb<56, 32, 8>(g, gc, xin, xc, xout, b, m, omega, s); break;
+    case 1: prolong_post_rb<24, 24, 8>(g, gc, xin, xc, xout, b, m, omega, s); break;
+    case 2: prolong_post_rb<56, 56, 16>(g, gc, xin, xc, xout, b, m, omega, s); break;
+    case 3: prolong_post_rb<24, 48, 8>(g, gc, xin, xc, xout, b, m, omega, s); break;
+    default: prolong_post_rb<56, 24, 8>(g, gc, xin, xc, xout, b, m, omega, s); break;
+  }
+}
+
+struct TuneEntry {
+  int shape;
+  double us;  // average launch time of the chosen shape
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, TuneEntry> g_tuned;  // (kernel, n, device) -> choice
+
+int tuned_shape(int kernel, int n) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned.find({kernel, n, dev});
+  return it == g_tuned.end() ? -1 : it->second.shape;
+}
+}  // namespace
+
 template <typename T>
 void launch_mg2_pre_restrict(const GridDesc& g, const GridDesc& gc, const T* xin, T* xout,
                              const T* b, const T* m, T* bc, double omega, int nu, int zero_init,
                              cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
     if (nu == kRBSweeps) {
-      // tile shapes from a timing sweep on GB300 (52 + 12 and 20 + 12 halo columns fill
-      // whole 32-lane column groups)
-      if (g.n > 513) pre_restrict_rb<52, 52, 16>(g, gc, xin, xout, b, m, bc, omega, zero_init, s);
-      else pre_restrict_rb<20, 32, 8>(g, gc, xin, xout, b, m, bc, omega, zero_init, s);
+      int c = tuned_shape(0, g.n);
+      if (c < 0) c = g.n > 513 ? 0 : 1;  // fixed rule from a timing sweep on GB300
+      pre_rb_shape(c, g, gc, xin, xout, b, m, bc, omega, zero_init, s);
       return;
     }
   }
@@ -642,8 +894,9 @@ void launch_mg2_prolong_post(const GridDesc& g, const GridDesc& gc, const T* xin
                              cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
     if (nu == kRBSweeps) {
-      if (g.n > 513) prolong_post_rb<56, 32, 8>(g, gc, xin, xc, xout, b, m, omega, s);
-      else prolong_post_rb<24, 24, 8>(g, gc, xin, xc, xout, b, m, omega, s);
+      int c = tuned_shape(1, g.n);
+      if (c < 0) c = g.n > 513 ? 0 : 1;
+      post_rb_shape(c, g, gc, xin, xc, xout, b, m, omega, s);
       return;
     }
   }
@@ -660,6 +913,84 @@ void launch_mg2_coarse(const MGCoarse<T>& cl, const T* btop, T* xtop, double ome
   k_mg2_coarse<T><<<1, 1024, sm, s>>>(cl, btop, xtop, (T)omega, nu_pre, nu_post, load_x);
 }
 
+bool mg2_is_tuned(int n) { return tuned_shape(0, n) >= 0 && tuned_shape(1, n) >= 0; }
+
+int mg2_autotune(const GridDesc& g, const GridDesc& gc, float* xa, float* xb, const float* b,
+                 const float* m, float* bc, const float* xc, double omega, cudaStream_t s) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return 1;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return 1;
+  }
+  constexpr int kReps = 16;
+  int rc = 0;
+  for (int kernel = 0; kernel < 2 && rc == 0; ++kernel) {
+    const int ncand = kernel == 0 ? kPreShapes : kPostShapes;
+    int best = -1;
+    float best_ms = 0.f;
+    for (int c = 0; c < ncand && rc == 0; ++c) {
+      auto run = [&] {
+        if (kernel == 0) pre_rb_shape(c, g, gc, xa, xb, b, m, bc, omega, 0, s);
+        else post_rb_shape(c, g, gc, xb, xc, xa, b, m, omega, s);
+      };
+      run();  // first launch: attributes, module load
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < kReps; ++r) run();
+      cudaEventRecord(e1, s);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = 1;
+        break;
+      }
+      count_launches(-(kReps + 1));  // tuning launches are not the solver's work
+      if (best < 0 || ms < best_ms) {
+        best = c;
+        best_ms = ms;
+      }
+    }
+    if (rc == 0 && best >= 0) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tuned[{kernel, g.n, dev}] = TuneEntry{best, 1000.0 * best_ms / kReps};
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  return rc;
+}
+
+int mg2_tune_set(int kernel, int n, int shape) {
+  if (kernel < 0 || kernel > 1 || n < 3) return 1;
+  if (shape >= (kernel == 0 ? kPreShapes : kPostShapes)) return 1;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (shape < 0) g_tuned.erase({kernel, n, dev});
+  else g_tuned[{kernel, n, dev}] = TuneEntry{shape, 0.0};
+  return 0;
+}
+
+int mg2_tune_report(char* buf, size_t len) {
+  std::string out;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const auto& kv : g_tuned) {
+    const int kernel = std::get<0>(kv.first), n = std::get<1>(kv.first);
+    char line[160];
+    std::snprintf(line, sizeof(line), "%s n=%d dev=%d: %s %.2f us\n",
+                  kernel == 0 ? "pre_restrict" : "prolong_post", n, std::get<2>(kv.first),
+                  kernel == 0 ? kPreShapeNames[kv.second.shape] : kPostShapeNames[kv.second.shape],
+                  kv.second.us);
+    out += line;
+  }
+  if (buf && len > 0) {
+    std::snprintf(buf, len, "%s", out.c_str());
+  }
+  return (int)out.size();
+}
+
 #define IPM_MG2_INST(T)                                                                           \
   template size_t mg2_coarse_smem<T>(const MGCoarse<T>&);                                        \
   template void launch_mg2_pre_restrict<T>(const GridDesc&, const GridDesc&, const T*, T*,       \
@@ -671,6 +1002,58 @@ void launch_mg2_coarse(const MGCoarse<T>& cl, const T* btop, T* xtop, double ome
                                      cudaStream_t);
 IPM_MG2_INST(float)
 IPM_MG2_INST(double)
+
+namespace {
+size_t mid_cycle_smem(const MidCycle& mc) {
+  size_t sm = RBShape<kMidPreTX, kMidPreTY, kRBSweeps + 2, kMidNW>::smem;
+  sm = std::max(sm, RBShape<kMidPostT, kMidPostT, kRBSweeps, kMidNW>::smem);
+  return std::max(sm, mg2_coarse_smem<float>(mc.cl));
+}
+}  // namespace
+
+int mg2_mid_blocks(const MidCycle& mc) {
+  int dev = 0, coop = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const size_t sm = mid_cycle_smem(mc);
+  ensure_smem_attr((const void*)k_mg2_mid_cycle, sm);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mg2_mid_cycle, kMidNW * 32, sm) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  int tiles = 1;
+  for (int l = 0; l < mc.nt; ++l) {
+    const int m = mc.g[l].n - 2;
+    const int pre = ((m + kMidPreTX - 1) / kMidPreTX) * ((m + kMidPreTY - 1) / kMidPreTY);
+    const int post = ((m + kMidPostT - 1) / kMidPostT) * ((m + kMidPostT - 1) / kMidPostT);
+    tiles = std::max(tiles, std::max(pre, post));
+  }
+  return std::min(tiles, per_sm * sms);
+}
+
+void launch_mg2_mid_cycle(const MidCycle& mc, GridBarrier* bar, double omega, int blocks,
+                          cudaStream_t s) {
+  const size_t sm = mid_cycle_smem(mc);
+  ensure_smem_attr((const void*)k_mg2_mid_cycle, sm);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(kMidNW * 32);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  count_launches(1);
+  cudaLaunchKernelEx(&cfg, k_mg2_mid_cycle, mc, bar, (float)omega);
+}
 
 // ---------------------------------------------------------------------------
 // Chebyshev semi-iteration for (M + Theta_y) x = b, temporally blocked (2D):

@@ -155,6 +155,51 @@ template <typename T>
 void launch_mg2_coarse(const MGCoarse<T>& cl, const T* btop, T* xtop, double omega, int nu_pre,
                        int nu_post, int load_x, cudaStream_t s);
 
+// Persistent form of the part of an FP32 V-cycle below the finest level (2D Poisson, 5
+// smoothing sweeps): one cooperative launch runs the pre-smoothing and restriction of the
+// tiled levels (finest first), the one-CTA cycle of the small levels, and the prolongation
+// and post-smoothing back up, with grid-wide barriers between the phases. The coarse
+// correction equation starts from zero on every level it covers.
+constexpr int kMaxMid = 8;
+struct MidCycle {
+  int nt;                      // tiled levels, finest first
+  GridDesc g[kMaxMid + 1];     // g[nt]: top level of the one-CTA part
+  float* xa[kMaxMid];          // iterate written by the post-smoothing of level l
+  float* xb[kMaxMid];          // scratch iterate: written by the pre-smoothing, read back
+  const float* b[kMaxMid];
+  const float* m[kMaxMid];
+  float* bnext[kMaxMid];       // right-hand side of the next coarser level (restriction)
+  MGCoarse<float> cl;          // levels of the one-CTA part (top level: b = bnext[nt - 1])
+  float* xcoarse;              // iterate of the one-CTA part's top level
+};
+// Grid-wide barrier state (zero-initialised device memory, one per stream of use). A block
+// that waits longer than a fixed spin budget sets `timeout`, writes NaN to the V-cycle's
+// output and leaves, so a failed barrier surfaces as a non-finite Krylov vector.
+struct GridBarrier {
+  unsigned count;
+  unsigned gen;
+  int timeout;
+  int pad;
+};
+// Tile-shape autotuning of the FP32 register-blocked pre- and post-smoothing kernels for the
+// grid of g: every candidate shape timed on the given buffers (xa, xb, the level's x
+// buffers; b, m its right-hand side and diagonal; bc, xc the next coarser level's
+// right-hand side and iterate; all overwritten but b, m, xc), the fastest kept for this
+// grid size and device for the rest of the process. Returns 0 on success.
+int mg2_autotune(const GridDesc& g, const GridDesc& gc, float* xa, float* xb, const float* b,
+                 const float* m, float* bc, const float* xc, double omega, cudaStream_t s);
+bool mg2_is_tuned(int n);
+// Text lines "kernel n=.. dev=..: shape time" of every choice made so far; returns the
+// length of the full text (buf may be NULL).
+int mg2_tune_report(char* buf, size_t len);
+// Pin (shape >= 0) or forget (shape < 0) the choice for kernel 0 (pre) / 1 (post) and grid
+// size n on the current device; returns 0, or 1 for an unknown kernel or shape.
+int mg2_tune_set(int kernel, int n, int shape);
+// Blocks the cooperative launch uses (0: cooperative launches unsupported on this device).
+int mg2_mid_blocks(const MidCycle& mc);
+void launch_mg2_mid_cycle(const MidCycle& mc, GridBarrier* bar, double omega, int blocks,
+                          cudaStream_t s);
+
 // Temporally blocked Chebyshev (2D): `ns` steps per launch with step weights omega[0..ns)
 constexpr int kMaxChebBlock = 8;
 struct ChebSteps {

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "ipm.h"
@@ -72,7 +73,7 @@ struct ipm_solver {
   // layout of the basis entries the kernels never write (boundary and padding nodes, which
   // must read as zero): -1 all zero, 0 FP64, 1 float-float
   int vlayout = -1;
-  double* mr[14] = {};
+  double* mr[16] = {};
   double* cheb64[4] = {};
   float* cheb32[4] = {};
   MGHier<double> mg64;
@@ -99,6 +100,8 @@ struct ipm_solver {
   long long prof_seen = 0;
   std::vector<cudaEvent_t> prof_ev;
   std::vector<int> prof_tag;
+  std::vector<double> prof_bp, prof_bo;  // algorithmic bytes of each sampled launch
+  double prof_bp_sum = 0.0, prof_bo_sum = 0.0;
   int prof_used = 0;
   double prof_ms = 0.0;
   long long prof_count = 0;
@@ -150,10 +153,12 @@ struct ipm_solver {
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, prof_ev[i], prof_ev[i + 1]));
       int tag = prof_tag[i / 2];
-      if (tag == 0 || tag == 13) {
+      if (tag == 0 || tag >= 13) {
         prof_ms += ms;
         ++prof_count;
         if (tag == 13) ++prof_zero;
+        prof_bp_sum += prof_bp[i / 2];
+        prof_bo_sum += prof_bo[i / 2];
       } else {
         ph_ms[tag] += ms;
         ++ph_count[tag];
@@ -169,6 +174,8 @@ struct ipm_solver {
         prof_ev.push_back(e);
       }
       prof_tag.assign(4096, 0);
+      prof_bp.assign(4096, 0.0);
+      prof_bo.assign(4096, 0.0);
     }
   }
   int prof_open = 0;  // event pairs begun but not yet ended
@@ -192,6 +199,30 @@ struct ipm_solver {
     --prof_open;
   }
   // sampled smoother timing (tag 0; tag 13 for launches that start from a zero iterate)
+  // kernel sampled by the profile hook: 0 finest-level pre-smoothing + restriction,
+  // 1 finest-level prolongation + post-smoothing, 2 persistent cycle below the finest level,
+  // 3 saddle operator
+  int prof_kind = 0;
+  // bp, bo: algorithmic bytes of the launch, per pass and once (ipm_profile_kernel_read)
+  int prof_begin_kind(int kind, int tag, double bp = 0.0, double bo = 0.0) {
+    if (kind != prof_kind) return -1;
+    int slot = prof_begin(tag);
+    if (slot >= 0) {
+      prof_bp[slot / 2] = bp;
+      prof_bo[slot / 2] = bo;
+    }
+    return slot;
+  }
+  // algorithmic bytes of the FP32 2D multigrid launches, from the unknowns of a level:
+  // a sweep reads x, b, M_hat and writes x (4 values per pass); the residual and
+  // restriction read x, b, M_hat and write the coarse right-hand side (4); prolongation
+  // and correction read x and the coarse x and write x (3). "Once": every value a launch
+  // needs, read or written once.
+  static double u2(int n) { return (double)(n - 2) * (n - 2); }
+  static double pre_pass(int n, int nu, bool zero) { return (4.0 * nu + 4.0 - zero) * u2(n) * 4; }
+  static double pre_once(int n, bool zero) { return (4.25 - zero) * u2(n) * 4; }
+  static double post_pass(int n, int nu) { return (3.0 + 4.0 * nu) * u2(n) * 4; }
+  static double post_once(int n) { return 4.25 * u2(n) * 4; }
   int prof_begin(int tag = 0) {
     if (!prof_on || phases_on || (prof_seen++ % prof_every) != 0) return -1;
     ensure_events();
@@ -476,7 +507,7 @@ struct ipm_solver {
     }
     bool z = zero_x;
     for (int i = 0; i < o.smooth_pre; ++i) {
-      int pr = (l == 0 && !z) ? prof_begin() : -1;
+      int pr = (l == 0 && !z) ? prof_begin_kind(0, 0) : -1;
       launch_mg_smooth<T>(L.g, opl(l), L.x[cur], L.x[1 - cur], L.b, L.m, L.jinv, z, tr, stream);
       prof_end(pr);
       cur = 1 - cur;
@@ -489,7 +520,7 @@ struct ipm_solver {
     vcycle(mg, l + 1, true, tr, o);
     launch_mg_prolong_add<T>(L.g, C.g, C.x[mg.cur[l + 1]], L.x[cur], stream);
     for (int i = 0; i < o.smooth_post; ++i) {
-      int pr = l == 0 ? prof_begin() : -1;
+      int pr = l == 0 ? prof_begin_kind(1, 14) : -1;
       launch_mg_smooth<T>(L.g, opl(l), L.x[cur], L.x[1 - cur], L.b, L.m, L.jinv, 0, tr, stream);
       prof_end(pr);
       cur = 1 - cur;
@@ -509,18 +540,107 @@ struct ipm_solver {
   bool fused_mg() const { return g.dim == 2 && fused && nu_fits && lvop.empty(); }
   bool nu_fits = true;  // fused tiles hold up to 8 sweeps of halo
 
+  // levels below the finest one in one persistent cooperative launch (FP32, 5 + 5 sweeps):
+  // levels above 33^2 as tiles, the rest in one CTA; returns false when not applicable
+  bool use_mid_cycle = false;  // kernel_flags bit 7 sets it
+  GridBarrier* gbar = nullptr;
+  int mid_blocks = -1;  // blocks of the cooperative launch (0: not available)
+#ifndef IPM_MID_TOP
+#define IPM_MID_TOP 129
+#endif
+  // levels [lt, nlev) of the mixed FP32 hierarchy in one persistent launch: levels above
+  // 33^2 (and at most IPM_MID_TOP per direction) as tiles, the rest in one CTA; the levels
+  // [0, lt) above keep one launch per level. Returns lt, or 0 when not applicable.
+  int prepare_mid(MGHier<float>& mg, const ipm_options& o, MidCycle& mc) {
+    if (!use_mid_cycle || o.smooth_pre != 5 || o.smooth_post != 5) return 0;
+    int lt = 1;
+    while (lt < mg.nlev && mg.lv[lt].g.n > IPM_MID_TOP) ++lt;
+    int lm = lt;
+    while (lm < mg.nlev && mg.lv[lm].g.n > 33) ++lm;
+    const int nt = lm - lt;  // tiled levels in the persistent launch
+    if (nt < 1 || nt > kMaxMid || mg.nlev - lm > kMaxCoarse) return 0;
+    mc.nt = nt;
+    for (int t = 0; t < nt; ++t) {
+      MGLevel<float>& L = mg.lv[lt + t];
+      mc.g[t] = L.g;
+      mc.xa[t] = L.x[mg.cur[lt + t]];
+      mc.xb[t] = L.x[1 - mg.cur[lt + t]];
+      mc.b[t] = L.b;
+      mc.m[t] = L.m;
+      mc.bnext[t] = mg.lv[lt + t + 1].b;
+    }
+    mc.g[nt] = mg.lv[lm].g;
+    mc.cl.nl = mg.nlev - lm;
+    for (int l = lm; l < mg.nlev; ++l) {
+      mc.cl.n[l - lm] = mg.lv[l].g.n;
+      mc.cl.pitch[l - lm] = mg.lv[l].g.pitch;
+      mc.cl.m[l - lm] = mg.lv[l].m;
+    }
+    mc.xcoarse = mg.lv[lm].x[mg.cur[lm]];
+    if (mid_blocks < 0) mid_blocks = mg2_mid_blocks(mc);
+    if (mid_blocks <= 0) return 0;
+    if (!gbar) gbar = alloc<GridBarrier>(1);
+    return lt;
+  }
+
   // one V-cycle with the fused kernels (same operator, smoother and transfers)
   template <typename T>
   void vcycle_fused(MGHier<T>& mg, bool zero_x, const ipm_options& o) {
+    if constexpr (std::is_same<T, float>::value) {
+      // the upper levels as their own launches, everything from IPM_MID_TOP down in one
+      // persistent launch
+      MidCycle mc;
+      const int lt = prepare_mid(mg, o, mc);
+      if (lt > 0) {
+        for (int l = 0; l < lt; ++l) {
+          MGLevel<float>& L = mg.lv[l];
+          int& cur = mg.cur[l];
+          const bool z = l > 0 || zero_x;
+          int pr = prof_begin_kind(l == 0 ? 0 : 4, l == 0 && zero_x ? 13 : 0,
+                                   pre_pass(L.g.n, o.smooth_pre, z), pre_once(L.g.n, z));
+          int ph = ph_begin(l == 0 ? 9 : 11);
+          launch_mg2_pre_restrict<float>(L.g, mg.lv[l + 1].g, L.x[cur], L.x[1 - cur], L.b, L.m,
+                                         mg.lv[l + 1].b, omega(), o.smooth_pre, z ? 1 : 0,
+                                         stream);
+          ph_end(ph);
+          prof_end(pr);
+          cur = 1 - cur;
+        }
+        double mbp = 0.0, mbo = 0.0;
+        for (int l = lt; l + 1 < mg.nlev; ++l) {
+          mbp += pre_pass(mg.lv[l].g.n, 5, true) + post_pass(mg.lv[l].g.n, 5);
+          mbo += pre_once(mg.lv[l].g.n, true) + post_once(mg.lv[l].g.n);
+        }
+        int pr2 = prof_begin_kind(2, 15, mbp, mbo);
+        int ph2 = ph_begin(12);
+        launch_mg2_mid_cycle(mc, gbar, omega(), mid_blocks, stream);
+        ph_end(ph2);
+        prof_end(pr2);
+        for (int l = lt - 1; l >= 0; --l) {
+          MGLevel<float>& L = mg.lv[l];
+          int& cur = mg.cur[l];
+          int pr3 = prof_begin_kind(l == 0 ? 1 : 4, 14, post_pass(L.g.n, 5), post_once(L.g.n));
+          int ph3 = ph_begin(l == 0 ? 10 : 11);
+          launch_mg2_prolong_post<float>(L.g, mg.lv[l + 1].g, L.x[cur], mg.lv[l + 1].x[mg.cur[l + 1]],
+                                         L.x[1 - cur], L.b, L.m, omega(), o.smooth_post, stream);
+          ph_end(ph3);
+          prof_end(pr3);
+          cur = 1 - cur;
+        }
+        return;
+      }
+    }
     const int lc = coarse_start(mg);
     for (int l = 0; l < lc; ++l) {
       MGLevel<T>& L = mg.lv[l];
       int& cur = mg.cur[l];
-      int pr = l == 0 ? prof_begin(zero_x ? 13 : 0) : -1;
+      const bool z = l > 0 || zero_x;
+      const int n = L.g.n;
+      int pr = prof_begin_kind(l == 0 ? 0 : 4, l == 0 && zero_x ? 13 : 0,
+                               pre_pass(n, o.smooth_pre, z), pre_once(n, z));
       int ph = ph_begin(l == 0 ? 9 : 11);
       launch_mg2_pre_restrict<T>(L.g, mg.lv[l + 1].g, L.x[cur], L.x[1 - cur], L.b, L.m,
-                                 mg.lv[l + 1].b, omega(), o.smooth_pre, (l > 0 || zero_x) ? 1 : 0,
-                                 stream);
+                                 mg.lv[l + 1].b, omega(), o.smooth_pre, z ? 1 : 0, stream);
       ph_end(ph);
       prof_end(pr);
       cur = 1 - cur;
@@ -534,17 +654,27 @@ struct ipm_solver {
     }
     // the one-CTA cycle starts from zero below the top level; when it is the top
     // level itself it continues from the current iterate after the first cycle
+    double cbp = 0.0, cbo = 0.0;
+    for (int l = lc; l + 1 < mg.nlev; ++l) {
+      cbp += pre_pass(mg.lv[l].g.n, o.smooth_pre, true) + post_pass(mg.lv[l].g.n, o.smooth_post);
+      cbo += u2(mg.lv[l].g.n) * 4 * (l == lc ? 3.0 : 1.0);  // b, x of the top; m of every level
+    }
+    int prc = prof_begin_kind(2, 15, cbp, cbo);
     int phc = ph_begin(12);
     launch_mg2_coarse<T>(cl, mg.lv[lc].b, mg.lv[lc].x[mg.cur[lc]], omega(), o.smooth_pre,
                          o.smooth_post, (lc == 0 && !zero_x) ? 1 : 0, stream);
     ph_end(phc);
+    prof_end(prc);
     for (int l = lc - 1; l >= 0; --l) {
       MGLevel<T>& L = mg.lv[l];
       int& cur = mg.cur[l];
+      int pr = prof_begin_kind(l == 0 ? 1 : 4, 14, post_pass(L.g.n, o.smooth_post),
+                               post_once(L.g.n));
       int ph = ph_begin(l == 0 ? 10 : 11);
       launch_mg2_prolong_post<T>(L.g, mg.lv[l + 1].g, L.x[cur], mg.lv[l + 1].x[mg.cur[l + 1]],
                                  L.x[1 - cur], L.b, L.m, omega(), o.smooth_post, stream);
       ph_end(ph);
+      prof_end(pr);
       cur = 1 - cur;
     }
   }
@@ -562,6 +692,22 @@ struct ipm_solver {
   void mg_setup_mixed() {
     mg_setup(mg32, dg.mh32);
     if (use_ff_outer()) launch_split3_ff(g, dg.mh, mgm3, mgm3 + F(), stream);
+    if (autotune && fused_mg()) autotune_tiles();
+  }
+
+  // tile shapes of the FP32 tiled levels: timed once per grid size and device in this
+  // process (kernel_flags bit 9 keeps the fixed shapes). Runs eagerly, before any capture,
+  // on this solver's level buffers, which the following cycle overwrites.
+  bool autotune = true;
+  void autotune_tiles() {
+    const int lc = coarse_start(mg32);
+    for (int l = 0; l < lc; ++l) {
+      MGLevel<float>& L = mg32.lv[l];
+      if (mg2_is_tuned(L.g.n)) continue;
+      MGLevel<float>& C = mg32.lv[l + 1];
+      if (mg2_autotune(L.g, C.g, L.x[0], L.x[1], L.b, L.m, C.b, C.x[0], omega(), stream) != 0)
+        throw IpmError{IPM_ECUDA, "tile autotuning failed"};
+    }
   }
 
   // float-float outer iterate (high part, then low part); right-hand side as FP64 (b64) or
@@ -810,7 +956,10 @@ struct ipm_solver {
   }
 
   void newton_apply(const double* x, double* y) {
+    const double ob = 11.0 * 8.0 * (double)nI();  // 7 fields read, 4 written, FP64
+    int pr = prof_begin_kind(3, 16, ob, ob);
     launch_newton_apply(g, problem(), dg, x, y, stream);
+    prof_end(pr);
   }
 
   double norm(const double* x, long long len) {
@@ -830,7 +979,7 @@ struct ipm_solver {
         vlayout = -1;
       }
     } else if (!mr[0]) {
-      for (int i = 0; i < 14; ++i) mr[i] = alloc<double>(f4);
+      for (int i = 0; i < 16; ++i) mr[i] = alloc<double>(f4);
     }
   }
 
@@ -855,7 +1004,10 @@ struct ipm_solver {
     if (pff_ok) precond_ff(vj, zj, o);
     else precond(ktmp, zj, tri, o);
     int p1 = ph_begin(6);
+    const double ob = 11.0 * 8.0 * (double)nI();
+    int pr = prof_begin_kind(3, 16, ob, ob);
     launch_newton_apply_ff(g, problem(), dg, zj, w, stream);
+    prof_end(pr);
     ph_end(p1);
     int p2 = ph_begin(7);
     launch_multidot_ff(Vf, sf, j + 1, w, len, part, kdev, kff, 1, stream);
@@ -1067,7 +1219,59 @@ struct ipm_solver {
     return hbuf[0];
   }
 
+  // MINRES with P_D. The all-FP64 path runs it once to krylov_tol. On the mixed path the
+  // preconditioner (FP32 Chebyshev, z-block and V-cycles) is symmetric only to FP32 accuracy,
+  // which bounds the residual MINRES's recurrences can certify; FP64 iterative refinement
+  // restores the tolerance: the true residual r = b - A x in FP64, a MINRES solve of
+  // A d = r to a moderate relative tolerance, x += d, until ||r|| <= krylov_tol ||b||.
   void minres(const ipm_options& o, const double* b, double* x, int* iters, double* relres) {
+    const long long len = 4 * F();
+    const bool refine = o.precision == IPM_PREC_MIXED && !(o.kernel_flags & 256);
+    double nb = norm(b, len);
+    *iters = 0;
+    *relres = 0.0;
+    if (nb == 0.0) {
+      CK(cudaMemsetAsync(x, 0, sizeof(double) * len, stream));
+      return;
+    }
+    if (!refine) {
+      *iters = minres_core(o, b, x, o.krylov_tol * nb, o.max_krylov);
+    } else {
+      double* rr = mr[13];
+      double* d = mr[14];
+      CK(cudaMemsetAsync(x, 0, sizeof(double) * len, stream));
+      launch_axpby(rr, b, 1.0, 0.0, len, stream);
+      double res = nb;
+      int total = 0;
+      const double tol = o.krylov_tol * nb;
+      for (int sweep = 0; sweep < kMaxRefine && total < o.max_krylov && res > tol; ++sweep) {
+        // inner tolerance: kRefineInner relative to the current residual, not below the target
+        const double inner = std::max(tol, kRefineInner * res);
+        total += minres_core(o, rr, d, inner, o.max_krylov - total);
+        launch_axpby(x, d, 1.0, 1.0, len, stream);
+        newton_apply(x, rr);
+        launch_axpby(rr, b, 1.0, -1.0, len, stream);  // rr = b - A x
+        const double nr = norm(rr, len);
+        if (!std::isfinite(nr)) throw IpmError{IPM_EBREAKDOWN, "non-finite refinement residual"};
+        if (nr >= res) {  // no progress: keep the previous iterate and stop
+          launch_axpby(x, d, -1.0, 1.0, len, stream);
+          break;
+        }
+        res = nr;
+      }
+      *iters = total;
+    }
+    newton_apply(x, ktmp);
+    launch_axpby(ktmp, b, 1.0, -1.0, len, stream);
+    *relres = norm(ktmp, len) / nb;
+  }
+
+  static constexpr int kMaxRefine = 12;
+  static constexpr double kRefineInner = 1e-4;
+
+  // preconditioned MINRES for A x = b from x = 0 until the recurrence residual is below
+  // tol_abs or after max_it iterations; returns the iterations taken
+  int minres_core(const ipm_options& o, const double* b, double* x, double tol_abs, int max_it) {
     long long len = 4 * F();
     double *v_prev = mr[0], *v_cur = mr[1], *v_next = mr[2], *z_cur = mr[3], *z_next = mr[4];
     double *w_prev = mr[5], *w_cur = mr[6], *w_next = mr[7], *Az = mr[8];
@@ -1077,18 +1281,16 @@ struct ipm_solver {
       CK(cudaMemsetAsync(p, 0, sizeof(double) * len, stream));
     launch_axpby(r, b, 1.0, 0.0, len, stream);
     launch_axpby(v_cur, b, 1.0, 0.0, len, stream);
-    *iters = 0;
-    *relres = 0.0;
     double nb = norm(b, len);
-    if (nb == 0.0) return;
+    if (nb == 0.0) return 0;
     precond(v_cur, z_cur, 0, o);
     double gam = std::sqrt(dot(z_cur, v_cur, len));
     double gam_prev = 1.0, eta = gam;
     double s_prev = 0, s_cur = 0, c_prev = 1, c_cur = 1;
-    double tol = o.krylov_tol * nb;
+    double tol = tol_abs;
     double res = nb;
     int j = 0;
-    while (j < o.max_krylov) {
+    while (j < max_it) {
       ++j;
       launch_axpby(z_cur, z_cur, 1.0 / gam, 0.0, len, stream);
       newton_apply(z_cur, Az);
@@ -1126,10 +1328,7 @@ struct ipm_solver {
       if (!std::isfinite(res)) throw IpmError{IPM_EBREAKDOWN, "non-finite MINRES residual"};
       if (res <= tol || gam == 0.0) break;
     }
-    newton_apply(x, ktmp);
-    launch_axpby(ktmp, b, 1.0, -1.0, len, stream);
-    *relres = norm(ktmp, len) / nb;
-    *iters = j;
+    return j;
   }
 
   void krylov(const ipm_options& o, const double* b, double* x, int* iters, double* relres) {
@@ -1177,6 +1376,8 @@ struct ipm_solver {
     ff_outer = (o.kernel_flags & 16) == 0;
     nu_fits = o.smooth_pre <= 8 && o.smooth_post <= 8;
     use_graphs = (o.kernel_flags & 2) == 0;
+    use_mid_cycle = (o.kernel_flags & 128) != 0;
+    autotune = (o.kernel_flags & 512) == 0;
   }
 
   int solve(const ipm_options& o, ipm_report* rep) {
@@ -1433,6 +1634,7 @@ int ipm_profile_smoother(ipm_solver* s, int enable, int every) {
   return guarded(s, [&] {
     s->prof_flush();
     s->prof_on = enable != 0;
+    s->prof_kind = 0;
     s->prof_every = every;
     s->prof_seen = 0;
     s->prof_ms = 0.0;
@@ -1479,6 +1681,44 @@ int ipm_profile_read(ipm_solver* s, double* total_ms, long long* launches, doubl
     if (bytes_per_launch) *bytes_per_launch = vals * (double)unknowns * word;
     return IPM_OK;
   });
+}
+
+int ipm_profile_kernel(ipm_solver* s, int kind, int enable, int every) {
+  if (!s || kind < 0 || kind > 4 || every < 1) return IPM_EINVAL;
+  return guarded(s, [&] {
+    s->prof_flush();
+    s->prof_on = enable != 0;
+    s->prof_kind = kind;
+    s->prof_every = every;
+    s->prof_seen = 0;
+    s->prof_ms = 0.0;
+    s->prof_count = 0;
+    s->prof_zero = 0;
+    s->prof_bp_sum = 0.0;
+    s->prof_bo_sum = 0.0;
+    return IPM_OK;
+  });
+}
+
+int ipm_profile_kernel_read(ipm_solver* s, double* total_ms, long long* sampled, long long* calls,
+                            double* bytes_pass, double* bytes_once) {
+  if (!s) return IPM_EINVAL;
+  return guarded(s, [&] {
+    s->prof_flush();
+    const double k = s->prof_count > 0 ? (double)s->prof_count : 1.0;
+    if (total_ms) *total_ms = s->prof_ms;
+    if (sampled) *sampled = s->prof_count;
+    if (calls) *calls = s->prof_seen;
+    if (bytes_pass) *bytes_pass = s->prof_bp_sum / k;
+    if (bytes_once) *bytes_once = s->prof_bo_sum / k;
+    return IPM_OK;
+  });
+}
+
+int ipm_tuning_report(char* buf, size_t len) { return mg2_tune_report(buf, len); }
+
+int ipm_tuning_set(int kernel, int n, int shape) {
+  return mg2_tune_set(kernel, n, shape) == 0 ? IPM_OK : IPM_EINVAL;
 }
 
 const char* ipm_last_error(const ipm_solver* s) {

@@ -30,7 +30,9 @@ EXPORTED = (
     "ipm_set_data_device", "ipm_solve", "ipm_get_state", "ipm_get_control", "ipm_get_adjoint",
     "ipm_get_state_device", "ipm_get_control_device", "ipm_get_adjoint_device",
     "ipm_get_history", "ipm_destroy", "ipm_launch_count",
-    "ipm_profile_smoother", "ipm_profile_read", "ipm_profile_phases", "ipm_strerror", "ipm_last_error",
+    "ipm_profile_smoother", "ipm_profile_read", "ipm_profile_phases", "ipm_profile_kernel",
+    "ipm_profile_kernel_read", "ipm_tuning_report", "ipm_tuning_set",
+    "ipm_strerror", "ipm_last_error",
     "ipm_newton_apply_device", "ipm_precond_apply_device", "ipm_chebyshev_device",
     "ipm_vcycle_device", "ipm_newton_step_device", "ipm_chebyshev_noalloc",
     "ipm_reset", "ipm_device_bytes", "ipm_server_create", "ipm_server_submit",
@@ -114,6 +116,12 @@ def load() -> C.CDLL:
     lib.ipm_profile_smoother.argtypes = [P, C.c_int, C.c_int]
     lib.ipm_profile_read.argtypes = [P, D, C.POINTER(C.c_longlong), D]
     lib.ipm_profile_phases.argtypes = [P, C.c_int, D, C.POINTER(C.c_longlong), C.c_int]
+    lib.ipm_profile_kernel.argtypes = [P, C.c_int, C.c_int, C.c_int]
+    lib.ipm_profile_kernel_read.argtypes = [P, D, C.POINTER(C.c_longlong),
+                                            C.POINTER(C.c_longlong), D, D]
+    lib.ipm_tuning_report.argtypes = [C.c_char_p, C.c_size_t]
+    lib.ipm_tuning_report.restype = C.c_int
+    lib.ipm_tuning_set.argtypes = [C.c_int, C.c_int, C.c_int]
     lib.ipm_strerror.argtypes = [C.c_int]
     lib.ipm_strerror.restype = C.c_char_p
     lib.ipm_last_error.argtypes = [P]
@@ -137,6 +145,22 @@ def load() -> C.CDLL:
     lib.ipm_server_destroy.restype = None
     _lib = lib
     return lib
+
+
+def tuning_report() -> str:
+    """Tile shapes the autotuner chose so far (one line per kernel and grid size)."""
+    lib = load()
+    n = lib.ipm_tuning_report(None, 0)
+    buf = C.create_string_buffer(n + 1)
+    lib.ipm_tuning_report(buf, n + 1)
+    return buf.value.decode()
+
+
+def tuning_set(kernel: int, n: int, shape: int):
+    """Pin (shape >= 0) or forget (shape < 0) a tile shape (see ipm_tuning_set)."""
+    rc = load().ipm_tuning_set(kernel, n, shape)
+    if rc != OK:
+        raise IpmError(rc, "unknown kernel or shape")
 
 
 def launch_count() -> int:
@@ -347,6 +371,24 @@ class Solver:
         by = C.c_double()
         self._check(self._lib.ipm_profile_read(self._h, C.byref(ms), C.byref(cnt), C.byref(by)))
         return ms.value, cnt.value, by.value
+
+    KERNELS = ("finest_pre_restrict", "finest_prolong_post", "coarse_cycle", "saddle_operator",
+               "mid_level_tiles")
+
+    def profile_kernel(self, kind: int, enable: bool, every: int = 4):
+        """Sample CUDA-event timings of one kernel (see KERNELS) on the solver's stream."""
+        self._check(self._lib.ipm_profile_kernel(self._h, kind, int(enable), every))
+
+    def profile_kernel_read(self) -> dict:
+        ms = C.c_double()
+        smp = C.c_longlong()
+        calls = C.c_longlong()
+        bp = C.c_double()
+        bo = C.c_double()
+        self._check(self._lib.ipm_profile_kernel_read(self._h, C.byref(ms), C.byref(smp),
+                                                      C.byref(calls), C.byref(bp), C.byref(bo)))
+        return dict(ms=ms.value, sampled=smp.value, calls=calls.value, bytes_pass=bp.value,
+                    bytes_once=bo.value)
 
     PHASES = ("", "chebyshev", "zblock+coupling", "multigrid", "mass_theta+convert",
               "normalise+norm", "newton_operator", "gs_dots", "gs_updates", "mg_fine_pre",

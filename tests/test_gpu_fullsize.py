@@ -55,12 +55,30 @@ def test_mixed_vcycle_tile_kernels(n):
     v = host(s.vcycle(False, md, bd, out, precision=ipm.PREC_MIXED))[qp.idx]
     v_sweep = host(s.vcycle(False, md, bd, out, precision=ipm.PREC_MIXED, kernel_flags=1))[qp.idx]
     v_o64 = host(s.vcycle(False, md, bd, out, precision=ipm.PREC_MIXED, kernel_flags=16))[qp.idx]
+    # one persistent cooperative launch for the levels from 129^2 down vs one launch per level
+    v_lvl = host(s.vcycle(False, md, bd, out, precision=ipm.PREC_MIXED, kernel_flags=128))[qp.idx]
     v64 = host(s.vcycle(False, md, bd, out))[qp.idx]
+    # every candidate tile shape of the autotuner computes the same cycle bit for bit
+    v_fixed = host(s.vcycle(False, md, bd, out, precision=ipm.PREC_MIXED, kernel_flags=512))[qp.idx]
+    assert np.array_equal(v, v_fixed)
+    assert f"pre_restrict n={n} " in ipm.tuning_report()  # the first mixed cycle tuned this grid
+    if n in (257, 1025):
+        levels = [n >> k | 1 for k in range(0, 4) if (n >> k | 1) > 65]
+        for shape in range(5):
+            for lv in levels:
+                ipm.tuning_set(0, lv, shape)
+                ipm.tuning_set(1, lv, shape)
+            vs = host(s.vcycle(False, md, bd, out, precision=ipm.PREC_MIXED))[qp.idx]
+            assert np.array_equal(vs, v), shape
+        for lv in levels:
+            ipm.tuning_set(0, lv, -1)
+            ipm.tuning_set(1, lv, -1)
     s.close()
     # the per-sweep FP32 kernels take the stiffness stencil as 8 x_c - (sum of 8), the fused
     # ones on differences (x_c - x_nb): both within FP32 reach of the FP64 cycles
     assert rel(v, v_sweep) < 1e-5
     assert rel(v, v_o64) < 2e-6  # float-float vs FP64 outer residual
+    assert rel(v, v_lvl) < 2e-6
     assert rel(v, v64) < 1e-5
     assert np.linalg.norm(b - A @ v) < 0.05 * np.linalg.norm(b)
     if n <= 513:

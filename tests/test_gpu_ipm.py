@@ -102,6 +102,22 @@ def test_mixed_precision_gaussian(cell, n):
         assert rel(got[f], want[f]) < 1e-6, (f, rel(got[f], want[f]))
 
 
+@pytest.mark.parametrize("make", [lambda: W.workload_c1(), lambda: W.workload_c2(n=65, cell=1),
+                                  lambda: W.workload_c2(n=129, cell=3)])
+def test_mixed_minres_with_refinement(make):
+    """MINRES + P_D on the mixed-precision path (FP32 Chebyshev, z-block and V-cycles) inside
+    FP64 iterative refinement: every Newton system reaches the FP64 tolerance on its true
+    residual, and the solve matches the oracle at the same mu^k within the mixed bar."""
+    wl = make()
+    common = wl.ya != -math.inf or wl.yb != math.inf
+    k = _iters_to(wl, 1e-6, common)
+    got, want, rep, _, _ = _run_pair(wl, k, common, krylov=ipm.KRYLOV_MINRES_PD,
+                                     precision=ipm.PREC_MIXED)
+    for f in ("y", "u", "p"):
+        assert rel(got[f], want[f]) < 1e-6, (f, rel(got[f], want[f]))
+    assert rep["krylov_relres_max"] < 1.5e-10
+
+
 def test_gap_mu_rule_matches_oracle():
     wl = W.workload_c2(n=33, cell=3)
     qp = Q.from_workload(wl)
