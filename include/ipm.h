@@ -54,14 +54,22 @@ typedef struct {
   int n[3];
 } ipm_grid;
 
-/* State equation: Poisson (Sections 5.1) or convection-diffusion with SUPG
+/* State equation: Poisson (Sections 5.1), convection-diffusion with SUPG
  * (Section 5.2; 2D only) with diffusion eps and the recirculating wind
- * w = (2 x2 (1 - x1^2), -2 x1 (1 - x2^2)) (wind = 0). */
-typedef enum { IPM_POISSON = 0, IPM_CONVDIFF_SUPG = 1 } ipm_pde_kind;
+ * w = (2 x2 (1 - x1^2), -2 x1 (1 - x2^2)) (wind = 0), or the heat equation
+ * y_t - Lap y = u + f on (0, T) (Section 3.4, all-at-once, backward Euler).
+ * IPM_HEAT: grid dim = 2 with n <= 65 nodes per direction; the time interval (0, T)
+ * is split into n - 2 steps of tau = T / (n - 2), so every nodal array holds n^3 values:
+ * n^2 per time level t_0 = 0, t_1, ..., t_{n-2} = T, then one unused level. The Dirichlet
+ * data g carries the initial state y_0 in level 0 (its other entries must be zero); y_d,
+ * f, the bounds and the results use levels 1 .. n-2. The cost and the L1 term integrate
+ * in time by the rectangle rule; no state bounds; GMRES + P_T only. */
+typedef enum { IPM_POISSON = 0, IPM_CONVDIFF_SUPG = 1, IPM_HEAT = 2 } ipm_pde_kind;
 typedef struct {
   int kind;
   double eps;
   int wind;
+  double T; /* final time (IPM_HEAT) */
 } ipm_pde;
 
 /* Bounds (Section 1, (box), (boxs)). Scalars, or nodal arrays when the pointer
@@ -76,6 +84,15 @@ typedef struct {
 enum { IPM_PREC_FP64 = 0, IPM_PREC_MIXED = 1 };
 enum { IPM_KRYLOV_MINRES_PD = 0, IPM_KRYLOV_GMRES_PT = 1 };
 enum { IPM_STOP_PAPER = 0, IPM_STOP_KKT = 1, IPM_STOP_FIXED = 2 };
+
+/* Partial observation (the subsection "Preconditioner for Partial Observations",
+ * Section 4): the tracking term 1/2 ||y - y_d||^2 integrates only over the elements whose
+ * centre lies strictly inside the box lo < x < hi (dim values each; the third is ignored
+ * in 2D), so the state row of (NewtonSystem) carries the singular mass M_s of the observed
+ * elements, and GMRES is preconditioned with P_Pi (three solves with L, L^T + M_l and
+ * L + M_r, Section 4), in FP64. lo = hi = NULL restores observation of the whole domain.
+ * Must precede ipm_set_data. IPM_EINVAL for a box with no element, or for the heat
+ * equation. Declared with the other solver calls below. */
 
 /* Solver options; ipm_default_options fills the paper's values (Section 5):
  * alpha0 = 0.995, eps_p = eps_d = eps_c = 1e-6, sigma = 0.2, mu0 = 1,
@@ -148,6 +165,8 @@ size_t ipm_device_bytes(const ipm_solver* s);
 /* Use an existing CUDA stream (cudaStream_t passed as void*; NULL = the
  * solver's own stream). All device work of later calls is ordered on it. */
 int ipm_set_stream(ipm_solver* s, void* cuda_stream);
+
+int ipm_set_observation(ipm_solver* s, const double* lo, const double* hi);
 
 /* Problem data (Section 1): desired state y_d, source f, Dirichlet data g
  * (boundary entries of g are used). Host arrays of n^d doubles; NULL = zero. */

@@ -20,6 +20,16 @@ struct GridDesc {
   long long plane;  // elements per z-plane (pitch * n)
   long long field;  // elements per field (plane for 2D, plane * n for 3D)
   double h;         // mesh size 1/(n-1)
+  // Space-time layout of the all-at-once heat equation (Section 3.4): a 2D grid of n^2
+  // nodes per time level stored as the z-planes of a dim-3 grid, plane k = time t_k
+  // (plane 0 the initial state, planes 1 .. n-2 the unknown levels, plane n-1 unused),
+  // with the time-level masses tau M and the backward-Euler operator below.
+  int heat;         // 0, or 1 for the space-time layout
+  double tau;       // time step (heat layout)
+  // Partial observation (the subsection on partial observations): per element, indexed by
+  // the element's lowest-corner node, 1 where the tracking term integrates, else 0; null =
+  // the whole domain. Only the tracking mass M_s of the state row uses it.
+  const float* obs;
 };
 
 IPM_HD long long node_index(const GridDesc& g, int i, int j, int k) {
@@ -34,6 +44,18 @@ inline GridDesc make_grid(int dim, int n) {
   g.plane = (long long)g.pitch * n;
   g.field = dim == 2 ? g.plane : g.plane * n;
   g.h = 1.0 / (n - 1);
+  g.heat = 0;
+  g.tau = 0.0;
+  g.obs = nullptr;
+  return g;
+}
+
+// The space-time grid of the heat equation: n^2 nodes per level, n - 2 time levels of
+// size tau.
+inline GridDesc make_heat_grid(int n, double tau) {
+  GridDesc g = make_grid(3, n);
+  g.heat = 1;
+  g.tau = tau;
   return g;
 }
 
@@ -123,11 +145,43 @@ struct Stencil {
   int dim;
   int p;
   long long pl;
-  T mscale;  // h^d / 6^d
+  T mscale;  // h^d / 6^d (heat layout: tau h^2 / 36, the time-level mass)
   T kscale;  // 1 (2D) or h (3D)
+  int heat;  // space-time layout: masses act within a time level
+  T tau;
+  T m2scale;  // h^2 / 36 (heat layout)
+  const float* obs;  // observed elements (partial observation), or null
+  // tracking mass M_s: the Q1 element masses M_e = (h/6)^d (x)_d [2 1; 1 2] of the observed
+  // elements around the node; the plain mass without an observation mask
+  template <typename F>
+  IPM_D T track_f(const F& f, long long c) const {
+    if (!obs) return mass_f(f, c);
+    T acc = T(0);
+    const int ne = dim == 3 ? 8 : 4;
+    for (int e = 0; e < ne; ++e) {
+      const int ea = e & 1, eb = (e >> 1) & 1, ec = (e >> 2) & 1;  // node's corner in the element
+      const long long base = c - ea - (long long)eb * p - (long long)ec * pl;
+      if (obs[base] == 0.f) continue;
+      for (int q = 0; q < ne; ++q) {
+        const int qa = q & 1, qb = (q >> 1) & 1, qc = (q >> 2) & 1;
+        T w = (qa == ea ? T(2) : T(1)) * (qb == eb ? T(2) : T(1));
+        if (dim == 3) w *= qc == ec ? T(2) : T(1);
+        acc += w * f(base + qa + (long long)qb * p + (long long)qc * pl);
+      }
+    }
+    return mscale * acc;
+  }
+  IPM_D T track(const T* __restrict__ x, long long c) const { return track_f(Ld<T>{x}, c); }
   template <typename F>
   IPM_D T mass_f(const F& f, long long c) const {
-    return mscale * (dim == 2 ? mass2_raw<T>(f, c, p) : mass3_raw<T>(f, c, p, pl));
+    return mscale * ((dim == 2 || heat) ? mass2_raw<T>(f, c, p) : mass3_raw<T>(f, c, p, pl));
+  }
+  // heat layout: the backward-Euler operator calL of Section 3.4 at time level k,
+  // (M + tau K) x_k - M x_{k-1}, and its transpose (M + tau K) x_k - M x_{k+1}
+  template <typename F>
+  IPM_D T heat_L(const F& f, long long c, int dir) const {
+    return m2scale * mass2_raw<T>(f, c, p) + tau * stiff2<T>(f, c, p) -
+           m2scale * mass2_raw<T>(f, c + dir * pl, p);
   }
   template <typename F>
   IPM_D T stiff_f(const F& f, long long c) const {
@@ -145,14 +199,21 @@ inline Stencil<T> make_stencil(const GridDesc& g) {
   s.pl = g.plane;
   s.mscale = g.dim == 2 ? T(g.h * g.h / 36.0) : T(g.h * g.h * g.h / 216.0);
   s.kscale = g.dim == 2 ? T(1) : T(g.h);
+  s.heat = g.heat;
+  s.tau = T(g.tau);
+  s.m2scale = T(g.h * g.h / 36.0);
+  if (g.heat) s.mscale = T(g.tau * g.h * g.h / 36.0);
+  s.obs = g.obs;
   return s;
 }
 
-inline double mass_diag(const GridDesc& g) {  // (2h/3)^d
+inline double mass_diag(const GridDesc& g) {  // (2h/3)^d; heat layout tau (2h/3)^2
   double t = 2.0 * g.h / 3.0;
+  if (g.heat) return g.tau * t * t;
   return g.dim == 2 ? t * t : t * t * t;
 }
-inline double lumped_mass(const GridDesc& g) {  // h^d
+inline double lumped_mass(const GridDesc& g) {  // h^d; heat layout tau h^2
+  if (g.heat) return g.tau * g.h * g.h;
   return g.dim == 2 ? g.h * g.h : g.h * g.h * g.h;
 }
 inline double stiff_diag(const GridDesc& g) {  // 8/3 (2D) or 8h/3 (3D)

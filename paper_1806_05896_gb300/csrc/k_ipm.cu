@@ -14,6 +14,7 @@ namespace {
 // ---------------------------------------------------------------------------
 template <typename T, typename F>
 IPM_D T apply_L(const OpL& L, const Stencil<T>& st, const F& f, long long c, long long field) {
+  if (st.heat) return st.heat_L(f, c, -1);
   if (L.coef == nullptr) return st.stiff_f(f, c);
   T acc = T(0);
 #pragma unroll
@@ -27,6 +28,7 @@ IPM_D T apply_L(const OpL& L, const Stencil<T>& st, const F& f, long long c, lon
 // coefficients are zero at non-interior nodes.
 template <typename T, typename F>
 IPM_D T apply_LT(const OpL& L, const Stencil<T>& st, const F& f, long long c, long long field) {
+  if (st.heat) return st.heat_L(f, c, +1);
   if (L.coef == nullptr) return st.stiff_f(f, c);
   T acc = T(0);
 #pragma unroll
@@ -98,7 +100,7 @@ __global__ void k_setup_data(GridDesc g, Stencil<double> st, const double* __res
   int i, j, k;
   long long c;
   if (!interior_node(g, i, j, k, c)) return;
-  cy[c] = st.mass_f(LdDiff<double>{yd, gl}, c);
+  cy[c] = st.track_f(LdDiff<double>{yd, gl}, c);
   fv[c] = st.mass(f, c) - apply_L<double>(L, st, Ld<double>{gl}, c, g.field);
 }
 
@@ -106,14 +108,17 @@ __global__ void k_setup_data(GridDesc g, Stencil<double> st, const double* __res
 __global__ void k_element_mass_form(GridDesc g, const double* __restrict__ yd,
                                     const double* __restrict__ gl, double* __restrict__ part) {
   __shared__ double sh[32];
+  // heat layout: the 2D elements of every time level 1 .. n-2, weighted by tau
+  const int edim = g.heat ? 2 : g.dim;
   long long ne1 = g.n - 1;
-  long long ne = g.dim == 3 ? ne1 * ne1 * ne1 : ne1 * ne1;
-  int nl = g.dim == 3 ? 8 : 4;
+  long long ne = g.heat ? ne1 * ne1 * (g.n - 2) : (g.dim == 3 ? ne1 * ne1 * ne1 : ne1 * ne1);
+  int nl = edim == 3 ? 8 : 4;
   double acc = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne;
        e += (long long)gridDim.x * blockDim.x) {
     int ex = (int)(e % ne1), ey = (int)((e / ne1) % ne1);
-    int ez = g.dim == 3 ? (int)(e / (ne1 * ne1)) : 0;
+    int ez = g.dim == 3 ? (int)(e / (ne1 * ne1)) + (g.heat ? 1 : 0) : 0;
+    if (g.obs && g.obs[node_index(g, ex, ey, ez)] == 0.f) continue;  // unobserved element
     double r[8];
     for (int l = 0; l < nl; ++l) {
       long long c = node_index(g, ex + (l & 1), ey + ((l >> 1) & 1), ez + ((l >> 2) & 1));
@@ -123,13 +128,13 @@ __global__ void k_element_mass_form(GridDesc g, const double* __restrict__ yd,
     for (int a = 0; a < nl; ++a)
       for (int bb = 0; bb < nl; ++bb) {
         double wgt = 1.0;
-        for (int kk = 0; kk < g.dim; ++kk) wgt *= (((a >> kk) & 1) == ((bb >> kk) & 1)) ? 2.0 : 1.0;
+        for (int kk = 0; kk < edim; ++kk) wgt *= (((a >> kk) & 1) == ((bb >> kk) & 1)) ? 2.0 : 1.0;
         q += wgt * r[a] * r[bb];
       }
     acc += q;
   }
   double s6 = g.h / 6.0;
-  double scale = g.dim == 3 ? s6 * s6 * s6 : s6 * s6;
+  double scale = g.heat ? g.tau * s6 * s6 : (g.dim == 3 ? s6 * s6 * s6 : s6 * s6);
   double t = block_sum(acc * scale, sh);
   if (lin_tid() == 0) part[lin_block()] = t;
 }
@@ -214,7 +219,7 @@ __global__ void k_prep(GridDesc g, Stencil<double> st, IpmProblem pb, IpmBounds 
     dg.thyff[c] = t.h;
     dg.thyff[F + c] = t.l;
   }
-  double My = st.mass(s.y, c);
+  double My = st.track(s.y, c);  // tracking mass: M, or M_s under partial observation
   double Mu = st.mass_f(LdDiff<double>{s.w, s.v}, c);
   double Mp = st.mass(s.p, c);
   double Ly = apply_L<double>(pb.L, st, Ld<double>{s.y}, c, F);
@@ -341,7 +346,7 @@ __global__ void k_residuals(GridDesc g, Stencil<double> st, IpmProblem pb, IpmBo
   if (in) {
     const long long F = g.field;
     double y = s.y[c], w = s.w[c], v = s.v[c];
-    double My = st.mass(s.y, c);
+    double My = st.track(s.y, c);
     double Mu = st.mass_f(LdDiff<double>{s.w, s.v}, c);
     double Mp = st.mass(s.p, c);
     double Ly = apply_L<double>(pb.L, st, Ld<double>{s.y}, c, F);
@@ -393,7 +398,7 @@ __global__ void k_newton_apply(GridDesc g, Stencil<double> st, IpmProblem pb, Ip
   const double* dw = x + F;
   const double* dv = x + 2 * F;
   const double* dp = x + 3 * F;
-  double My = st.mass(dy, c);
+  double My = st.track(dy, c);
   double Mp = st.mass(dp, c);
   double Ms = st.mass_f(LdDiff<double>{dw, dv}, c);
   double Ly = apply_L<double>(pb.L, st, Ld<double>{dy}, c, F);

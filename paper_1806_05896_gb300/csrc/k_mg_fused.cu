@@ -428,6 +428,136 @@ __global__ void __launch_bounds__(NW * 32) k_mg2_prolong_post_rb(GridDesc g, Gri
 // ---------------------------------------------------------------------------
 // One CTA, all coarse levels in shared memory (dense n x n per level).
 // ---------------------------------------------------------------------------
+// one damped-Jacobi sweep over the interior of an n x n level (threads as 32 x 32 grid)
+template <typename T>
+IPM_D void cta_sweep(const T* cur, T* nxt, const T* sb, const T* sm, const T* sj, int n, int zero) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
+  for (int iy = 1 + ty; iy < n - 1; iy += ny)
+    for (int ix = 1 + tx; ix < n - 1; ix += 32) {
+      const int i = iy * n + ix;
+      T xc = zero ? T(0) : cur[i];
+      T ax = zero ? T(0) : apply_A(cur, i, n, sm[i]);
+      nxt[i] = xc + sj[i] * (sb[i] - ax);
+    }
+}
+
+// the V-cycle on the levels of cl for the Q1 stiffness + diag(m) (cl.general == 0): every
+// level by the whole CTA, threads as a 32 x (blockDim / 32) grid
+template <typename T>
+IPM_D void coarse_cycle_box(const MGCoarse<T>& cl, const T* __restrict__ btop,
+                            T* __restrict__ xtop, T omega, int nu_pre, int nu_post, int load_x,
+                            unsigned char* smem_raw) {
+  T* base = reinterpret_cast<T*>(smem_raw);
+  // per-level size and offset of the six arrays (x0, x1, b, r, m, jinv) in a shared table,
+  // and the current-iterate parity of every level as a register bit mask: indexing
+  // per-thread arrays by the runtime level index would put them in local memory
+  __shared__ int s_n[kMaxCoarse], s_off[kMaxCoarse];  // (per kernel, shared with coarse_cycle)
+  if (threadIdx.x == 0) {
+    int off = 0;
+    for (int l = 0; l < cl.nl; ++l) {
+      s_n[l] = cl.n[l];
+      s_off[l] = off;
+      off += 6 * cl.n[l] * cl.n[l];
+    }
+  }
+  __syncthreads();
+  const int total = s_off[cl.nl - 1] + 6 * s_n[cl.nl - 1] * s_n[cl.nl - 1];
+  auto arr = [&](int l, int a) { return base + s_off[l] + a * s_n[l] * s_n[l]; };
+  enum { AX0 = 0, AX1 = 1, AB = 2, AR = 3, AM = 4, AJ = 5 };
+  // zero everything, then load b (top level) and m (all levels), interior entries
+  for (int t = threadIdx.x; t < total; t += blockDim.x) base[t] = T(0);
+  __syncthreads();
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
+  for (int l = 0; l < cl.nl; ++l) {
+    const int n = s_n[l];
+    T* Ml = arr(l, AM);
+    T* Jl = arr(l, AJ);
+    const T* mg = cl.m[l];
+    const long long pl = cl.pitch[l];
+    for (int iy = 1 + ty; iy < n - 1; iy += ny)
+      for (int ix = 1 + tx; ix < n - 1; ix += 32) {
+        T mm = mg[(long long)iy * pl + ix];
+        Ml[iy * n + ix] = mm;
+        Jl[iy * n + ix] = omega / (T(8.0 / 3.0) + mm);
+        if (l == 0) arr(0, AB)[iy * n + ix] = btop[(long long)iy * cl.pitch[0] + ix];
+        if (l == 0 && load_x) arr(0, AX0)[iy * n + ix] = xtop[(long long)iy * cl.pitch[0] + ix];
+      }
+  }
+  __syncthreads();
+  unsigned cur = 0;  // bit l: level l's current iterate is x1
+  auto xcur = [&](int l) { return arr(l, ((cur >> l) & 1u) ? AX1 : AX0); };
+  auto xnxt = [&](int l) { return arr(l, ((cur >> l) & 1u) ? AX0 : AX1); };
+  const int L = cl.nl - 1;
+  for (int l = 0; l < L; ++l) {
+    const int n = s_n[l];
+    const T* Bl = arr(l, AB);
+    const T* Ml = arr(l, AM);
+    const T* Jl = arr(l, AJ);
+    T* Rl = arr(l, AR);
+    for (int s = 0; s < nu_pre; ++s) {
+      cta_sweep(xcur(l), xnxt(l), Bl, Ml, Jl, n, s == 0 && !(l == 0 && load_x));
+      cur ^= 1u << l;
+      __syncthreads();
+    }
+    {
+      const T* c = xcur(l);
+      for (int iy = 1 + ty; iy < n - 1; iy += ny)
+        for (int ix = 1 + tx; ix < n - 1; ix += 32) {
+          const int i = iy * n + ix;
+          Rl[i] = Bl[i] - apply_A(c, i, n, Ml[i]);
+        }
+    }
+    __syncthreads();
+    {
+      const int nc = s_n[l + 1];
+      T* Bc = arr(l + 1, AB);
+      for (int J = 1 + ty; J < nc - 1; J += ny)
+        for (int I = 1 + tx; I < nc - 1; I += 32) {
+          const int i = (2 * J) * n + 2 * I;
+          const T* r = Rl;
+          T r0 = T(0.5) * r[i - n - 1] + r[i - n] + T(0.5) * r[i - n + 1];
+          T r1 = T(0.5) * r[i - 1] + r[i] + T(0.5) * r[i + 1];
+          T r2 = T(0.5) * r[i + n - 1] + r[i + n] + T(0.5) * r[i + n + 1];
+          Bc[J * nc + I] = T(0.5) * r0 + r1 + T(0.5) * r2;
+        }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {  // coarsest grid: 3 nodes per direction, one unknown
+    const int i = 1 * 3 + 1;
+    arr(L, AX0)[i] = arr(L, AB)[i] / (T(8.0 / 3.0) + arr(L, AM)[i]);
+  }
+  cur &= ~(1u << L);
+  __syncthreads();
+  for (int l = L - 1; l >= 0; --l) {
+    const int n = s_n[l], nc = s_n[l + 1];
+    T* c = xcur(l);
+    const T* xcs = xcur(l + 1);
+    const bool wipe = nu_pre == 0 && !(l == 0 && load_x);  // x never written on this level
+    for (int iy = 1 + ty; iy < n - 1; iy += ny)
+      for (int ix = 1 + tx; ix < n - 1; ix += 32) {
+        T base_v = wipe ? T(0) : c[iy * n + ix];
+        c[iy * n + ix] = base_v + prolong_at(xcs, nc, ix, iy);
+      }
+    __syncthreads();
+    const T* Bl = arr(l, AB);
+    const T* Ml = arr(l, AM);
+    const T* Jl = arr(l, AJ);
+    for (int s = 0; s < nu_post; ++s) {
+      cta_sweep(xcur(l), xnxt(l), Bl, Ml, Jl, n, 0);
+      cur ^= 1u << l;
+      __syncthreads();
+    }
+  }
+  {
+    const int n = s_n[0];
+    const T* c = xcur(0);
+    for (int iy = 1 + ty; iy < n - 1; iy += ny)
+      for (int ix = 1 + tx; ix < n - 1; ix += 32) xtop[(long long)iy * cl.pitch[0] + ix] = c[iy * n + ix];
+  }
+}
+
+
 // Work split of one level: the m = n - 2 interior columns times R row groups of K
 // consecutive rows; thread t < m R owns column c = t % m, rows 1 + g K ... of group g = t / m.
 // A thread reads its column and the two beside it once per row of its window (K + 2 rows)
@@ -457,11 +587,47 @@ IPM_D Strip strip_of(int n, int nthreads) {
 
 // mode 0: one damped-Jacobi sweep into out; mode 1: residual b - A x into out.
 // zero: the iterate is zero (first sweep from x = 0).
+// a constant symmetric 9-point stencil (centre, edge, corner weights)
+template <typename T>
+struct Stencil9 {
+  bool on;
+  T c0, ce, cc;
+};
+
 template <typename T>
 IPM_D void strip_pass(const T* __restrict__ cur, T* __restrict__ out, const T* __restrict__ sb,
                       const T* __restrict__ sm, const T* __restrict__ sj, int n, const Strip& st,
-                      int mode, bool zero) {
+                      int mode, bool zero, const Stencil9<T>& s9 = Stencil9<T>{false, T(0), T(0), T(0)}) {
   if (!st.active) return;
+  if (s9.on && !zero) {
+    // x_c, the horizontal pair sum l + r of each window row
+    const int ix = st.c + 1;
+    T lr[kCoarseK + 2], xm[kCoarseK + 2];
+#pragma unroll
+    for (int k = 0; k < kCoarseK + 2; ++k) {
+      const int iy = st.iy0 - 1 + k;
+      lr[k] = T(0);
+      xm[k] = T(0);
+      if (k < st.K + 2 && iy <= n - 1) {
+        const T* r = cur + iy * n + ix;
+        xm[k] = r[0];
+        lr[k] = r[-1] + r[1];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kCoarseK; ++k) {
+      const int iy = st.iy0 + k;
+      if (k < st.K && iy <= n - 2) {
+        const int i = iy * n + ix;
+        const T xc = xm[k + 1];
+        const T edges = (lr[k + 1] + xm[k]) + xm[k + 2];
+        const T corners = lr[k] + lr[k + 2];
+        const T ax = (s9.c0 * xc + s9.ce * edges + s9.cc * corners) + sm[i] * xc;
+        out[i] = mode == 0 ? xc + sj[i] * (sb[i] - ax) : sb[i] - ax;
+      }
+    }
+    return;
+  }
   const int ix = st.c + 1;
   if (zero) {
 #pragma unroll
@@ -545,7 +711,7 @@ IPM_D void coarse_cycle(const MGCoarse<T>& cl, const T* __restrict__ btop, T* __
       for (int ix = 1 + tx; ix < n - 1; ix += 32) {
         T mm = mg[(long long)iy * pl + ix];
         Ml[iy * n + ix] = mm;
-        Jl[iy * n + ix] = omega / (T(8.0 / 3.0) + mm);
+        Jl[iy * n + ix] = omega / ((cl.general ? cl.c0[l] : T(8.0 / 3.0)) + mm);
         if (l == 0) arr(0, AB)[iy * n + ix] = btop[(long long)iy * cl.pitch[0] + ix];
         if (l == 0 && load_x) arr(0, AX0)[iy * n + ix] = xtop[(long long)iy * cl.pitch[0] + ix];
       }
@@ -558,9 +724,11 @@ IPM_D void coarse_cycle(const MGCoarse<T>& cl, const T* __restrict__ btop, T* __
   int ls = 0;  // first small level
   while (ls < L && s_n[ls] > kCoarseSmallN) ++ls;
 
+  auto s9of = [&](int l) { return Stencil9<T>{cl.general != 0, cl.c0[l], cl.ce[l], cl.cc[l]}; };
   // pre-smoothing, residual and full-weighting restriction of level l
   auto descend = [&](int l, bool small) {
     const int n = s_n[l];
+    const Stencil9<T> s9 = s9of(l);
     const int nthr = small ? kCoarseSmallThreads : (int)blockDim.x;
     const Strip st = strip_of(n, nthr);
     const T* Bl = arr(l, AB);
@@ -568,11 +736,11 @@ IPM_D void coarse_cycle(const MGCoarse<T>& cl, const T* __restrict__ btop, T* __
     const T* Jl = arr(l, AJ);
     T* Rl = arr(l, AR);
     for (int s = 0; s < nu_pre; ++s) {
-      strip_pass(xcur(l), xnxt(l), Bl, Ml, Jl, n, st, 0, s == 0 && !(l == 0 && load_x));
+      strip_pass(xcur(l), xnxt(l), Bl, Ml, Jl, n, st, 0, s == 0 && !(l == 0 && load_x), s9);
       cur ^= 1u << l;
       coarse_sync(small);
     }
-    strip_pass(xcur(l), Rl, Bl, Ml, Jl, n, st, 1, false);
+    strip_pass(xcur(l), Rl, Bl, Ml, Jl, n, st, 1, false, s9);
     coarse_sync(small);
     const int nc = s_n[l + 1];
     T* Bc = arr(l + 1, AB);
@@ -611,8 +779,9 @@ IPM_D void coarse_cycle(const MGCoarse<T>& cl, const T* __restrict__ btop, T* __
     const T* Bl = arr(l, AB);
     const T* Ml = arr(l, AM);
     const T* Jl = arr(l, AJ);
+    const Stencil9<T> s9 = s9of(l);
     for (int s = 0; s < nu_post; ++s) {
-      strip_pass(xcur(l), xnxt(l), Bl, Ml, Jl, n, st, 0, false);
+      strip_pass(xcur(l), xnxt(l), Bl, Ml, Jl, n, st, 0, false, s9);
       cur ^= 1u << l;
       coarse_sync(small);
     }
@@ -623,7 +792,7 @@ IPM_D void coarse_cycle(const MGCoarse<T>& cl, const T* __restrict__ btop, T* __
     for (int l = ls; l < L; ++l) descend(l, true);
     if (threadIdx.x == 0) {  // coarsest grid: 3 nodes per direction, one unknown
       const int i = 1 * 3 + 1;
-      arr(L, AX0)[i] = arr(L, AB)[i] / (T(8.0 / 3.0) + arr(L, AM)[i]);
+      arr(L, AX0)[i] = arr(L, AB)[i] / ((cl.general ? cl.c0[L] : T(8.0 / 3.0)) + arr(L, AM)[i]);
     }
     cur &= ~(1u << L);
     coarse_sync(true);
@@ -646,6 +815,15 @@ template <typename T>
 __global__ void __launch_bounds__(1024) k_mg2_coarse(MGCoarse<T> cl, const T* __restrict__ btop,
                                                      T* __restrict__ xtop, T omega, int nu_pre,
                                                      int nu_post, int load_x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  coarse_cycle_box<T>(cl, btop, xtop, omega, nu_pre, nu_post, load_x, smem_raw);
+}
+
+// the same cycle for a constant 9-point stencil per level (cl.general == 1)
+template <typename T>
+__global__ void __launch_bounds__(1024) k_mg2_coarse9(MGCoarse<T> cl, const T* __restrict__ btop,
+                                                      T* __restrict__ xtop, T omega, int nu_pre,
+                                                      int nu_post, int load_x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   coarse_cycle<T>(cl, btop, xtop, omega, nu_pre, nu_post, load_x, smem_raw);
 }
@@ -709,8 +887,8 @@ __global__ void __launch_bounds__(kMidNW * 32) k_mg2_mid_cycle(MidCycle mc, Grid
   }
   if (ok) {
     if (blockIdx.x == 0)
-      coarse_cycle<float>(mc.cl, mc.bnext[mc.nt - 1], mc.xcoarse, omega, kRBSweeps, kRBSweeps, 0,
-                          smem_raw);
+      coarse_cycle_box<float>(mc.cl, mc.bnext[mc.nt - 1], mc.xcoarse, omega, kRBSweeps,
+                              kRBSweeps, 0, smem_raw);
     ok = grid_barrier(bar, nb);
   }
   for (int l = mc.nt - 1; l >= 0 && ok; --l) {
@@ -908,9 +1086,14 @@ template <typename T>
 void launch_mg2_coarse(const MGCoarse<T>& cl, const T* btop, T* xtop, double omega, int nu_pre,
                        int nu_post, int load_x, cudaStream_t s) {
   size_t sm = mg2_coarse_smem(cl);
-  ensure_smem_attr((const void*)k_mg2_coarse<T>, sm);
   count_launches(1);
-  k_mg2_coarse<T><<<1, 1024, sm, s>>>(cl, btop, xtop, (T)omega, nu_pre, nu_post, load_x);
+  if (cl.general) {
+    ensure_smem_attr((const void*)k_mg2_coarse9<T>, sm);
+    k_mg2_coarse9<T><<<1, 1024, sm, s>>>(cl, btop, xtop, (T)omega, nu_pre, nu_post, load_x);
+  } else {
+    ensure_smem_attr((const void*)k_mg2_coarse<T>, sm);
+    k_mg2_coarse<T><<<1, 1024, sm, s>>>(cl, btop, xtop, (T)omega, nu_pre, nu_post, load_x);
+  }
 }
 
 bool mg2_is_tuned(int n) { return tuned_shape(0, n) >= 0 && tuned_shape(1, n) >= 0; }

@@ -69,7 +69,9 @@ __global__ void k_coupling(GridDesc g, Stencil<double> st, OpL L, const double* 
   double v = -rp[c];
   if (triangular) {
     double ly;
-    if (L.coef == nullptr) {
+    if (st.heat) {
+      ly = st.heat_L(Ld<double>{zy}, c, -1);
+    } else if (L.coef == nullptr) {
       ly = st.stiff(zy, c);
     } else {
       ly = 0.0;
@@ -175,6 +177,43 @@ __global__ void k_convert(long long n, const Ti* __restrict__ x, To* __restrict_
     y[t] = (To)x[t];
 }
 
+
+// ---------------------------------------------------------------------------
+// Partial observation: P_Pi (the subsection on partial observations)
+// ---------------------------------------------------------------------------
+// diagonals of the V-cycle operators of S_Pi_hat = (L^T + M_l) L^{-1} (L + M_r):
+// m_l = row sums of M_s + Theta_y (the observed element masses lumped), and
+// m_r = D zeta D, the lumped M_bar Z^{-1} M_bar^T with the z-block Z = alpha D~_M + Theta_z,
+// zeta = (theta_w + theta_v) / (a (theta_w + theta_v) + theta_w theta_v), a = alpha D_M
+__global__ void k_pi_diags(GridDesc g, double a, double d, const double* __restrict__ thy,
+                           const double* __restrict__ thw, const double* __restrict__ thv,
+                           double* __restrict__ ml, double* __restrict__ mr) {
+  int i, j, k;
+  long long c;
+  if (!interior_node(g, i, j, k, c)) return;
+  const long long p = g.pitch, pl = g.plane;
+  const int ne = g.dim == 3 ? 8 : 4;
+  int nobs = 0;
+  for (int e = 0; e < ne; ++e) {
+    const long long base = c - (e & 1) - ((e >> 1) & 1) * p - ((e >> 2) & 1) * pl;
+    nobs += g.obs == nullptr || g.obs[base] != 0.f;
+  }
+  const double elem_row = g.dim == 3 ? g.h * g.h * g.h / 8.0 : g.h * g.h / 4.0;  // (h/2)^d
+  ml[c] = nobs * elem_row + thy[c];
+  const double tw = thw[c], tv = thv[c];
+  mr[c] = d * d * (tw + tv) / (a * (tw + tv) + tw * tv);
+}
+
+// out = (M_s + Theta_y) x - r
+__global__ void k_track_theta_minus(GridDesc g, Stencil<double> st, const double* __restrict__ x,
+                                    const double* __restrict__ thy, const double* __restrict__ r,
+                                    double* __restrict__ out) {
+  int i, j, k;
+  long long c;
+  if (!interior_node(g, i, j, k, c)) return;
+  out[c] = st.track(x, c) + thy[c] * x[c] - r[c];
+}
+
 }  // namespace
 
 template <typename T>
@@ -269,3 +308,16 @@ template void launch_mass_theta<float>(const GridDesc&, const float*, const floa
 template void launch_convert<double, float>(const GridDesc&, const double*, float*, cudaStream_t);
 template void launch_convert<float, double>(const GridDesc&, const float*, double*, cudaStream_t);
 template void launch_convert<double, double>(const GridDesc&, const double*, double*, cudaStream_t);
+
+void launch_pi_diags(const GridDesc& g, double a, double d, const double* thy, const double* thw,
+                     const double* thv, double* ml, double* mr, cudaStream_t s) {
+  count_launches(1);
+  k_pi_diags<<<interior_grid(g), interior_block(), 0, s>>>(g, a, d, thy, thw, thv, ml, mr);
+}
+
+void launch_track_theta_minus(const GridDesc& g, const double* x, const double* thy,
+                              const double* r, double* out, cudaStream_t s) {
+  count_launches(1);
+  k_track_theta_minus<<<interior_grid(g), interior_block(), 0, s>>>(g, make_stencil<double>(g), x,
+                                                                      thy, r, out);
+}

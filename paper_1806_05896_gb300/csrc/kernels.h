@@ -97,6 +97,12 @@ void launch_coupling(const GridDesc& g, OpL L, const double* zy, const double* z
                      const double* rp, int triangular, T* t, cudaStream_t s);
 template <typename T>
 void launch_mass_theta(const GridDesc& g, const T* x, const T* thy, T* out, cudaStream_t s);
+// partial observation: diagonals m_l, m_r of the V-cycle operators of S_Pi_hat, and
+// out = (M_s + Theta_y) x - r
+void launch_pi_diags(const GridDesc& g, double a, double d, const double* thy, const double* thw,
+                     const double* thv, double* ml, double* mr, cudaStream_t s);
+void launch_track_theta_minus(const GridDesc& g, const double* x, const double* thy,
+                              const double* r, double* out, cudaStream_t s);
 template <typename Ti, typename To>
 void launch_convert(const GridDesc& g, const Ti* x, To* y, cudaStream_t s);
 
@@ -140,6 +146,10 @@ struct MGCoarse {  // levels handled inside one CTA, finest first
   int n[kMaxCoarse];
   long long pitch[kMaxCoarse];
   const T* m[kMaxCoarse];
+  // general = 0: the Q1 stiffness (8/3 centre, -1/3 neighbours) + diag(m); general = 1: a
+  // constant symmetric 9-point stencil per level (centre, edge, corner weights) + diag(m)
+  int general;
+  T c0[kMaxCoarse], ce[kMaxCoarse], cc[kMaxCoarse];
 };
 template <typename T>
 size_t mg2_coarse_smem(const MGCoarse<T>& cl);
@@ -199,6 +209,15 @@ int mg2_tune_set(int kernel, int n, int shape);
 int mg2_mid_blocks(const MidCycle& mc);
 void launch_mg2_mid_cycle(const MidCycle& mc, GridBarrier* bar, double omega, int blocks,
                           cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// k_heat.cu (all-at-once heat equation, space-time layout of make_heat_grid)
+// ----------------------------------------------------------------------------
+// b32 plane k = t plane k + M (plane kp of x32) (kp < 0: t alone); plane kp of x32 -> x64
+void launch_heat_plane_rhs(const GridDesc& g, const double* t, int k, int kp, const float* x32,
+                           double* x64, float* b32, cudaStream_t s);
+void launch_heat_plane_store(const GridDesc& g, int k, const float* x32, double* x64,
+                             cudaStream_t s);
 
 // Temporally blocked Chebyshev (2D): `ns` steps per launch with step weights omega[0..ns)
 constexpr int kMaxChebBlock = 8;

@@ -40,7 +40,7 @@ using Key = std::tuple<int, int, int, long long>;  // dim, n, kind, eps bits
 
 Key key_of(const ipm_request& r) {
   long long eb = 0;
-  double e = r.pde.kind == IPM_CONVDIFF_SUPG ? r.pde.eps : 0.0;
+  double e = r.pde.kind == IPM_CONVDIFF_SUPG ? r.pde.eps : r.pde.kind == IPM_HEAT ? r.pde.T : 0.0;
   std::memcpy(&eb, &e, sizeof(eb));
   return Key{r.grid.dim, r.grid.n[0], r.pde.kind, eb};
 }
@@ -50,8 +50,9 @@ Key key_of(const ipm_request& r) {
 size_t estimate_bytes(const ipm_request& r) {
   const long long n = r.grid.n[0];
   const long long pitch = (n + 31) / 32 * 32;
-  const long long F = r.grid.dim == 2 ? pitch * n : pitch * n * n;
-  const long long nodes = r.grid.dim == 2 ? n * n : n * n * n;
+  const bool plane = r.grid.dim == 2 && r.pde.kind != IPM_HEAT;  // heat: n time levels
+  const long long F = plane ? pitch * n : pitch * n * n;
+  const long long nodes = plane ? n * n : n * n * n;
   const long long restart = r.opt.restart > 0 ? r.opt.restart : 50;
   double mg = r.grid.dim == 2 ? 4.0 / 3.0 : 8.0 / 7.0;
   double fields = 21 + 3 * 4 + 4 + 2 + 3 + 2 + 4  // state, data, diagonals, Krylov, buffers
@@ -208,7 +209,8 @@ int ipm_server_submit(ipm_server* sv, const ipm_request* rq, long long* ticket) 
   Request* r = new Request();
   r->rq = *rq;
   long long n = rq->grid.n[0];
-  r->yd.assign(rq->yd, rq->yd + (rq->grid.dim == 2 ? n * n : n * n * n));
+  const bool plane = rq->grid.dim == 2 && rq->pde.kind != IPM_HEAT;
+  r->yd.assign(rq->yd, rq->yd + (plane ? n * n : n * n * n));
   r->rq.yd = nullptr;
   r->need = estimate_bytes(*rq);
   r->t_submit = Clock::now();

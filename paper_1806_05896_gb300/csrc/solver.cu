@@ -317,12 +317,15 @@ struct ipm_solver {
       throw IpmError{IPM_EINVAL, "nodes per direction must be 2^k + 1 (k >= 1)"};
     if (!(a > 0.0) || !(b >= 0.0) || !std::isfinite(a) || !std::isfinite(b))
       throw IpmError{IPM_EINVAL, "need alpha > 0 and beta >= 0"};
-    pde = p ? *p : ipm_pde{IPM_POISSON, 1.0, 0};
-    if (pde.kind != IPM_POISSON && pde.kind != IPM_CONVDIFF_SUPG)
+    pde = p ? *p : ipm_pde{IPM_POISSON, 1.0, 0, 0.0};
+    if (pde.kind != IPM_POISSON && pde.kind != IPM_CONVDIFF_SUPG && pde.kind != IPM_HEAT)
       throw IpmError{IPM_EINVAL, "unknown state equation"};
     if (pde.kind == IPM_CONVDIFF_SUPG && (dim != 2 || !(pde.eps > 0.0) || pde.wind != 0))
       throw IpmError{IPM_EINVAL, "convection-diffusion needs dim 2, eps > 0 and wind 0"};
-    g = make_grid(dim, n);
+    if (pde.kind == IPM_HEAT && (dim != 2 || n < 5 || n > 65 || !(pde.T > 0.0) ||
+                                 !std::isfinite(pde.T)))
+      throw IpmError{IPM_EINVAL, "heat equation needs dim 2, 5 <= n <= 65 and T > 0"};
+    g = pde.kind == IPM_HEAT ? make_heat_grid(n, pde.T / (n - 2)) : make_grid(dim, n);
     alpha = a;
     beta = b;
     CK(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
@@ -381,7 +384,176 @@ struct ipm_solver {
     kdev = alloc<double>(4 * (kMaxRestart + 2));
     kff = alloc<float>(2 * 4 * (kMaxRestart + 2));
     dense = alloc<double>(nn());
+    if (heat()) build_heat_mg();
     set_bounds(bd);
+  }
+
+  // ------------------------------------------------------------------------
+  // Heat equation (Section 3.4), space-time layout: the hierarchy of one time level for
+  // the level-by-level solves with M + tau K + diag(M_hat_k) in the Schur approximation.
+  // ------------------------------------------------------------------------
+  struct HeatMG {
+    int nl = 0;
+    GridDesc lg[kMaxCoarse];
+    float* m[kMaxCoarse] = {};  // diag(M_hat) of every time level on each 2D level
+    float* b32 = nullptr;       // right-hand side and iterate of the level being solved
+    float* x32 = nullptr;
+  } hmg;
+  bool heat() const { return g.heat != 0; }
+
+  void build_heat_mg() {
+    int n = g.n, l = 0;
+    while (true) {
+      if (l >= kMaxCoarse) throw IpmError{IPM_EINVAL, "heat: too many levels"};
+      hmg.lg[l] = make_grid(2, n);
+      // level 0 reads the FP32 copy of M_hat of all time levels in place (plane stride
+      // g.plane = field of the 2D grid); coarser levels hold n time levels each
+      hmg.m[l] = l == 0 ? dg.mh32 : alloc<float>((long long)g.n * hmg.lg[l].field);
+      ++l;
+      if (n == 3) break;
+      n = (n - 1) / 2 + 1;
+    }
+    hmg.nl = l;
+    hmg.b32 = alloc<float>(F());
+    hmg.x32 = alloc<float>(F());
+  }
+
+  // per IPM step: M_hat restricted to the coarser 2D levels of every time level
+  void heat_setup() {
+    for (int k = 1; k <= g.n - 2; ++k)
+      for (int l = 1; l < hmg.nl; ++l)
+        launch_mg_restrict<float>(hmg.lg[l - 1], hmg.lg[l], hmg.m[l - 1] + k * hmg.lg[l - 1].field,
+                                  hmg.m[l] + k * hmg.lg[l].field, stream);
+  }
+
+  // x = (calL + M_hat)^{-1} t (forward in time) or (calL + M_hat)^{-T} t (backward): per time
+  // level a 2D solve with M + tau K + diag(M_hat_k), `vcycles` FP32 V-cycles of the one-CTA
+  // kernel, for the right-hand side t_k + M x_{k -+ 1}
+  void heat_lm_solve(const double* t, double* x, bool transpose, const ipm_options& o) {
+    const int nt = g.n - 2;
+    MGCoarse<float> cl;
+    cl.nl = hmg.nl;
+    cl.general = 1;
+    for (int l = 0; l < hmg.nl; ++l) {
+      const double H = hmg.lg[l].h;
+      cl.n[l] = hmg.lg[l].n;
+      cl.pitch[l] = hmg.lg[l].pitch;
+      // M + tau K on level l (Galerkin-consistent rediscretisation: the Q1 stiffness does
+      // not scale with the mesh in 2D, the mass scales with H^2)
+      cl.c0[l] = (float)(16.0 * H * H / 36.0 + 8.0 * g.tau / 3.0);
+      cl.ce[l] = (float)(4.0 * H * H / 36.0 - g.tau / 3.0);
+      cl.cc[l] = (float)(H * H / 36.0 - g.tau / 3.0);
+    }
+    const int cycles = std::max(1, o.vcycles);
+    int k = 0;
+    for (int step = 0; step < nt; ++step) {
+      k = transpose ? nt - step : 1 + step;
+      const int kp = step == 0 ? -1 : (transpose ? k + 1 : k - 1);
+      launch_heat_plane_rhs(g, t, k, kp, hmg.x32, x, hmg.b32, stream);
+      for (int l = 0; l < hmg.nl; ++l) cl.m[l] = hmg.m[l] + k * hmg.lg[l].field;
+      for (int c = 0; c < cycles; ++c)
+        launch_mg2_coarse<float>(cl, hmg.b32 + k * g.plane, hmg.x32 + k * g.plane, 0.8,
+                                 o.smooth_pre, o.smooth_post, c > 0 ? 1 : 0, stream);
+    }
+    launch_heat_plane_store(g, k, hmg.x32, x, stream);
+  }
+
+  // ------------------------------------------------------------------------
+  // Partial observation (the subsection on partial observations): the tracking term
+  // integrates over the elements whose centre lies strictly inside a box; the state row
+  // then carries M_s, which is singular, and GMRES is preconditioned with P_Pi.
+  // ------------------------------------------------------------------------
+  float* obs_dev = nullptr;
+  double *pim_l = nullptr, *pim_r = nullptr, *zero64 = nullptr;
+
+  void set_observation(const double* lo, const double* hi) {
+    if (heat()) throw IpmError{IPM_EINVAL, "partial observation is not defined for the heat equation"};
+    drop_graphs();  // captured launches carry the grid descriptor
+    has_data = false;
+    solved = false;
+    if (!lo || !hi) {
+      g.obs = nullptr;
+      return;
+    }
+    if (!obs_dev) {
+      obs_dev = alloc<float>(F());
+      pim_l = alloc<double>(F());
+      pim_r = alloc<double>(F());
+      zero64 = alloc<double>(F());
+    }
+    const int n = g.n, ne = n - 1;
+    std::vector<float> mask((size_t)F(), 0.f);
+    long long observed = 0;
+    for (int ez = 0; ez < (g.dim == 3 ? ne : 1); ++ez)
+      for (int ey = 0; ey < ne; ++ey)
+        for (int ex = 0; ex < ne; ++ex) {
+          const double cx = (ex + 0.5) * g.h, cyy = (ey + 0.5) * g.h, cz = (ez + 0.5) * g.h;
+          bool in = cx > lo[0] && cx < hi[0] && cyy > lo[1] && cyy < hi[1];
+          if (g.dim == 3) in = in && cz > lo[2] && cz < hi[2];
+          if (in) {
+            mask[(size_t)node_index(g, ex, ey, g.dim == 3 ? ez : 0)] = 1.f;
+            ++observed;
+          }
+        }
+    if (observed == 0) throw IpmError{IPM_EINVAL, "the observation box contains no element"};
+    CK(cudaMemcpyAsync(obs_dev, mask.data(), sizeof(float) * mask.size(), cudaMemcpyHostToDevice,
+                       stream));
+    sync();  // the host mask goes out of scope
+    g.obs = obs_dev;
+  }
+
+  // z = P_Pi^{-1} r: the permuted block-triangular preconditioner applied by three solves,
+  // v2 = Z^{-1} r_z, v1 = L^{-1} (M_bar v2 + r_p), v3 = S_Pi_hat^{-1} ((M_s + Theta_y) v1 - r_y),
+  // S_Pi_hat^{-1} = (L + M_r)^{-1} L (L^T + M_l)^{-1}; every inverse by V-cycles (M_l, M_r
+  // lumped to diagonals for the smoother's operator)
+  void precond_pi(const double* r, double* z, const ipm_options& o) {
+    const long long f = F();
+    int p2 = ph_begin(2);
+    launch_zblock(g, alpha * mass_diag(g), r + f, r + 2 * f, dg.thw, dg.thv, z + f, z + 2 * f,
+                  stream);
+    // t = -(M z_w - M z_v + r_p)
+    launch_coupling<double>(g, opL(), zero64, z + f, z + 2 * f, r + 3 * f, 1, mg64.lv[0].b, stream);
+    ph_end(p2);
+    int p3 = ph_begin(3);
+    mg_setup(mg64, zero64);
+    const double* x1 = mg_solve(mg64, 0, o);
+    launch_axpby(z, x1, -1.0, 0.0, f, stream);  // v1 = -L^{-1} t
+    mg_setup(mg64, pim_l);
+    launch_track_theta_minus(g, z, dg.thy, r, mg64.lv[0].b, stream);
+    const double* a1 = mg_solve(mg64, 1, o);
+    launch_coupling<double>(g, opL(), a1, zero64, zero64, zero64, 1, mg64.lv[0].b, stream);
+    mg_setup(mg64, pim_r);
+    const double* c1 = mg_solve(mg64, 0, o);
+    launch_convert<double, double>(g, c1, z + 3 * f, stream);
+    ph_end(p3);
+  }
+
+  // P^{-1} r for the heat equation (P_T of Section 4 with the time-dependent Schur
+  // approximation of Section 3.4): Chebyshev for tau calM + Theta_y, the pointwise z-block
+  // with tau D_M, the coupling with calL, and the level-by-level solves with calL + M_hat
+  void precond_heat(const double* r, double* z, int tri, const ipm_options& o) {
+    const long long f = F();
+    const bool mixed_cheb = o.precision == IPM_PREC_MIXED && !(o.kernel_flags & 4);
+    int p1 = ph_begin(1);
+    if (mixed_cheb) cheb_apply<float, double>(r, dg.thy32, z, o.cheb_steps, cheb32);
+    else cheb_apply<double, double>(r, dg.thy, z, o.cheb_steps, cheb64);
+    ph_end(p1);
+    int p2 = ph_begin(2);
+    launch_zblock(g, alpha * mass_diag(g), r + f, r + 2 * f, dg.thw, dg.thv, z + f, z + 2 * f,
+                  stream);
+    double* t = mg64.lv[0].b;
+    double* s1 = mg64.lv[0].r;
+    launch_coupling<double>(g, opL(), z, z + f, z + 2 * f, r + 3 * f, tri, t, stream);
+    ph_end(p2);
+    int p3 = ph_begin(3);
+    heat_lm_solve(t, s1, false, o);
+    ph_end(p3);
+    int p4 = ph_begin(4);
+    launch_mass_theta<double>(g, s1, dg.thy, t, stream);
+    ph_end(p4);
+    int p5 = ph_begin(3);
+    heat_lm_solve(t, z + 3 * f, true, o);
+    ph_end(p5);
   }
 
   // convection-diffusion: the SUPG operator rediscretised on every multigrid level, each
@@ -435,6 +607,8 @@ struct ipm_solver {
         throw IpmError{IPM_EINVAL, "state bounds must satisfy y_a < y_b"};
       if (yav[t] == INFINITY || ybv[t] == -INFINITY)
         throw IpmError{IPM_EINVAL, "state bounds are infeasible"};
+      if (heat() && (std::isfinite(yav[t]) || std::isfinite(ybv[t])))
+        throw IpmError{IPM_EINVAL, "the heat equation takes control bounds only"};
     }
     for (long long t = 0; t < m; ++t) {
       ub[t] = std::max(ub[t], 0.0);
@@ -571,6 +745,7 @@ struct ipm_solver {
     }
     mc.g[nt] = mg.lv[lm].g;
     mc.cl.nl = mg.nlev - lm;
+    mc.cl.general = 0;
     for (int l = lm; l < mg.nlev; ++l) {
       mc.cl.n[l - lm] = mg.lv[l].g.n;
       mc.cl.pitch[l - lm] = mg.lv[l].g.pitch;
@@ -646,6 +821,7 @@ struct ipm_solver {
       cur = 1 - cur;
     }
     MGCoarse<T> cl;
+    cl.general = 0;
     cl.nl = mg.nlev - lc;
     for (int l = lc; l < mg.nlev; ++l) {
       cl.n[l - lc] = mg.lv[l].g.n;
@@ -810,7 +986,9 @@ struct ipm_solver {
       cheb_apply_fused<T>(r, thy, (double*)z, steps, buf);
       return;
     }
-    double lmin = g.dim == 2 ? 0.25 : 0.125, lmax = g.dim == 2 ? 2.25 : 3.375;
+    // Q1 element bounds of D_M^{-1} M; the heat layout's masses act within a 2D time level
+    const bool d2 = g.dim == 2 || heat();
+    double lmin = d2 ? 0.25 : 0.125, lmax = d2 ? 2.25 : 3.375;
     double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sig = theta / delta;
     T* bT = buf[2];
     T* cur = buf[0];
@@ -834,6 +1012,14 @@ struct ipm_solver {
 
   // z = P^{-1} r, P = P_T (tri) or P_D (Section 4.2)
   void precond(const double* r, double* z, int tri, const ipm_options& o) {
+    if (heat()) {
+      precond_heat(r, z, tri, o);
+      return;
+    }
+    if (g.obs) {
+      precond_pi(r, z, o);
+      return;
+    }
     long long f = F();
     // kernel_flags bits 2 / 3 keep the Chebyshev and z-block / multigrid stage in FP64 on
     // the mixed path
@@ -951,6 +1137,15 @@ struct ipm_solver {
   }
 
   void setup_precond(const ipm_options& o) {
+    if (heat()) {
+      heat_setup();
+      return;
+    }
+    if (g.obs) {
+      launch_pi_diags(g, alpha * mass_diag(g), lumped_mass(g), dg.thy, dg.thw, dg.thv, pim_l,
+                      pim_r, stream);
+      return;
+    }
     if (o.precision == IPM_PREC_MIXED && !(o.kernel_flags & 8)) mg_setup_mixed();
     else mg_setup(mg64, dg.mh);
   }
@@ -1388,6 +1583,10 @@ struct ipm_solver {
         !(o.sigma > 0 && o.sigma < 1) || !(o.alpha0 > 0 && o.alpha0 < 1) || !(o.mu0 > 0) ||
         o.max_krylov < 1 || o.max_ipm < 0 || o.mu_rule < 0 || o.mu_rule > 1)
       throw IpmError{IPM_EINVAL, "invalid solver options"};
+    if (heat() && o.krylov != IPM_KRYLOV_GMRES_PT)
+      throw IpmError{IPM_EINVAL, "the heat equation is solved with GMRES + P_T"};
+    if (g.obs && (o.krylov != IPM_KRYLOV_GMRES_PT || o.precision != IPM_PREC_FP64))
+      throw IpmError{IPM_EINVAL, "partial observation is solved with GMRES + P_Pi in FP64"};
     if (o.smooth_pre != o.smooth_post && o.krylov == IPM_KRYLOV_MINRES_PD)
       throw IpmError{IPM_EINVAL, "MINRES needs a symmetric V-cycle (smooth_pre == smooth_post)"};
     auto t0 = std::chrono::steady_clock::now();
@@ -1416,7 +1615,8 @@ struct ipm_solver {
         break;
       }
       mu = o.mu_rule == 1 ? o.sigma * mean_prod : o.sigma * mu;
-      launch_prep(g, problem(), bounds(), st, dg, mu, rhs, o.precision == IPM_PREC_MIXED, stream);
+      launch_prep(g, problem(), bounds(), st, dg, mu, rhs, o.precision == IPM_PREC_MIXED || heat(),
+                  stream);
       setup_precond(o);
       int kit = 0;
       double krr = 0.0;
@@ -1711,6 +1911,14 @@ int ipm_profile_kernel_read(ipm_solver* s, double* total_ms, long long* sampled,
     if (calls) *calls = s->prof_seen;
     if (bytes_pass) *bytes_pass = s->prof_bp_sum / k;
     if (bytes_once) *bytes_once = s->prof_bo_sum / k;
+    return IPM_OK;
+  });
+}
+
+int ipm_set_observation(ipm_solver* s, const double* lo, const double* hi) {
+  if (!s || (!lo) != (!hi)) return IPM_EINVAL;
+  return guarded(s, [&] {
+    s->set_observation(lo, hi);
     return IPM_OK;
   });
 }

@@ -20,7 +20,8 @@ OK, EINVAL, ENOMEM, ENOTCONV, EBREAKDOWN, ETIMEOUT, ECUDA, ESTATE = range(8)
 PREC_FP64, PREC_MIXED = 0, 1
 KRYLOV_MINRES_PD, KRYLOV_GMRES_PT = 0, 1
 STOP_PAPER, STOP_KKT, STOP_FIXED = 0, 1, 2
-POISSON, CONVDIFF_SUPG = 0, 1
+POISSON, CONVDIFF_SUPG, HEAT = 0, 1, 2
+KINDS = {"poisson": POISSON, "cd": CONVDIFF_SUPG, "heat": HEAT}
 
 HIST_COLS = ("k", "mu", "xi_p", "xi_d", "xi_c", "kkt_rel", "alpha_P", "alpha_D",
              "krylov_iters", "krylov_relres")
@@ -31,7 +32,7 @@ EXPORTED = (
     "ipm_get_state_device", "ipm_get_control_device", "ipm_get_adjoint_device",
     "ipm_get_history", "ipm_destroy", "ipm_launch_count",
     "ipm_profile_smoother", "ipm_profile_read", "ipm_profile_phases", "ipm_profile_kernel",
-    "ipm_profile_kernel_read", "ipm_tuning_report", "ipm_tuning_set",
+    "ipm_profile_kernel_read", "ipm_tuning_report", "ipm_tuning_set", "ipm_set_observation",
     "ipm_strerror", "ipm_last_error",
     "ipm_newton_apply_device", "ipm_precond_apply_device", "ipm_chebyshev_device",
     "ipm_vcycle_device", "ipm_newton_step_device", "ipm_chebyshev_noalloc",
@@ -45,7 +46,7 @@ class Grid(C.Structure):
 
 
 class Pde(C.Structure):
-    _fields_ = [("kind", C.c_int), ("eps", C.c_double), ("wind", C.c_int)]
+    _fields_ = [("kind", C.c_int), ("eps", C.c_double), ("wind", C.c_int), ("T", C.c_double)]
 
 
 class Bounds(C.Structure):
@@ -122,6 +123,7 @@ def load() -> C.CDLL:
     lib.ipm_tuning_report.argtypes = [C.c_char_p, C.c_size_t]
     lib.ipm_tuning_report.restype = C.c_int
     lib.ipm_tuning_set.argtypes = [C.c_int, C.c_int, C.c_int]
+    lib.ipm_set_observation.argtypes = [P, D, D]
     lib.ipm_strerror.argtypes = [C.c_int]
     lib.ipm_strerror.restype = C.c_char_p
     lib.ipm_last_error.argtypes = [P]
@@ -219,7 +221,7 @@ class Server:
         o = options if options is not None else default_options(**kw)
         yd = np.ascontiguousarray(np.asarray(yd, dtype=np.float64).reshape(-1))
         rq = Request(Grid(dim, (C.c_int * 3)(n, n, n if dim == 3 else 0)),
-                     Pde(POISSON if kind == "poisson" else CONVDIFF_SUPG, eps, 0), alpha, beta,
+                     Pde(KINDS[kind], eps, 0, 0.0), alpha, beta,
                      Bounds(ua, ub, ya, yb, None, None, None, None),
                      yd.ctypes.data_as(C.POINTER(C.c_double)), o)
         t = C.c_longlong()
@@ -266,12 +268,14 @@ class Solver:
     """One problem instance on the current CUDA device (owns its device memory)."""
 
     def __init__(self, dim: int, n: int, alpha: float, beta: float, ua, ub,
-                 ya=-math.inf, yb=math.inf, kind: str = "poisson", eps: float = 1.0):
+                 ya=-math.inf, yb=math.inf, kind: str = "poisson", eps: float = 1.0,
+                 T: float = 1.0):
         lib = load()
         self._lib = lib
         self.dim, self.n = dim, n
         g = Grid(dim, (C.c_int * 3)(n, n, n if dim == 3 else 0))
-        pde = Pde(POISSON if kind == "poisson" else CONVDIFF_SUPG, eps, 0)
+        pde = Pde(KINDS[kind], eps, 0, T)
+        self.nodal_dim = 3 if kind == "heat" else dim
         keep = []
 
         def bnd(v):
@@ -297,7 +301,7 @@ class Solver:
 
     @property
     def nodes(self) -> int:
-        return self.n ** self.dim
+        return self.n ** self.nodal_dim
 
     def close(self):
         if getattr(self, "_h", None):
@@ -326,6 +330,15 @@ class Solver:
     def set_stream(self, stream_handle: Optional[int]):
         self._check(self._lib.ipm_set_stream(self._h, stream_handle))
 
+    def set_observation(self, lo=None, hi=None):
+        """Observe only the elements whose centre lies in the box lo < x < hi (None: all)."""
+        if lo is None:
+            self._check(self._lib.ipm_set_observation(self._h, None, None))
+            return
+        a = (C.c_double * 3)(*[float(v) for v in lo] + [0.0] * (3 - len(lo)))
+        b = (C.c_double * 3)(*[float(v) for v in hi] + [0.0] * (3 - len(hi)))
+        self._check(self._lib.ipm_set_observation(self._h, a, b))
+
     def set_data(self, yd=None, f=None, g=None):
         """Host nodal arrays (n^d, C order, x fastest); None = zero."""
         args = [_hptr(a) for a in (yd, f, g)]
@@ -345,7 +358,7 @@ class Solver:
         out = np.empty(self.nodes)
         self._check(getattr(self._lib, name)(self._h, out.ctypes.data_as(C.POINTER(C.c_double)),
                                              out.size))
-        return out.reshape((self.n,) * self.dim)
+        return out.reshape((self.n,) * self.nodal_dim)
 
     def state(self):
         return self._get("ipm_get_state")
