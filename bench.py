@@ -332,7 +332,7 @@ def run_ours(args, rank, world):
     def opts(prec, common=1):
         return ipm.default_options(precision=prec, krylov=ipm.KRYLOV_GMRES_PT, stop=ipm.STOP_KKT,
                                    kkt_tol=1e-6, restart=50, max_krylov=200, common_step=common,
-                                   max_ipm=60)
+                                   max_ipm=60, kernel_flags=args.kernel_flags)
 
     def timed(prec, steps, warmup, e2e=False, common=1):
         """`steps` solves after `warmup` untimed ones, rotating over this rank's cells in the
@@ -706,6 +706,9 @@ def main():
     ap.add_argument("--legs", default="all", choices=["all", "mixed"])
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--cells", type=int, default=0, help="sweep cells per rank (0 = all nine)")
+    ap.add_argument("--kernel-flags", type=int, default=0,
+                    help="ipm_options.kernel_flags of the timed solves (profiler runs pin the "
+                         "tile shapes with 512: timings under a profiler mislead the autotuner)")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--sweep-table", default="",
                     help="comma-separated grid sizes: print a sweep table and exit")

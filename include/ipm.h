@@ -237,8 +237,9 @@ int ipm_profile_phases(ipm_solver* s, int enable, double* ms, long long* counts,
 int ipm_tuning_report(char* buf, size_t len);
 /* Pin the tile shape of kernel 0 (pre-smoothing + restriction) or 1 (prolongation +
  * post-smoothing) for grid size n on the current device (shape = index into the
- * candidates: pre 52x52/16w, 20x32/8w, 52x32/8w, 52x24/8w, 20x64/8w; post 56x32/8w,
- * 24x24/8w, 56x56/16w, 24x48/8w, 56x24/8w), or forget it (shape < 0) so that the next solve
+ * candidates: pre 52x52/16w, 20x32/8w, 52x32/8w, 52x24/8w, 20x64/8w, 20x18/8w, 20x36/16w;
+ * post 56x32/8w, 24x24/8w, 56x56/16w, 24x48/8w, 56x24/8w, 24x16/8w, 24x40/16w), or forget
+ * it (shape < 0) so that the next solve
  * tunes again. For reproducible kernel selection. IPM_EINVAL for an unknown kernel/shape. */
 int ipm_tuning_set(int kernel, int n, int shape);
 const char* ipm_strerror(int code);

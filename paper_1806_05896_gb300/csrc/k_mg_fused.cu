@@ -991,11 +991,11 @@ void prolong_post_rb(const GridDesc& g, const GridDesc& gc, const float* xin, co
 // of the timing sweep that chose the defaults applies.
 // ---------------------------------------------------------------------------
 namespace {
-constexpr int kPreShapes = 5, kPostShapes = 5;
+constexpr int kPreShapes = 7, kPostShapes = 7;
 const char* const kPreShapeNames[kPreShapes] = {"52x52/16w", "20x32/8w", "52x32/8w", "52x24/8w",
-                                                "20x64/8w"};
+                                                "20x64/8w", "20x18/8w", "20x36/16w"};
 const char* const kPostShapeNames[kPostShapes] = {"56x32/8w", "24x24/8w", "56x56/16w", "24x48/8w",
-                                                  "56x24/8w"};
+                                                  "56x24/8w", "24x16/8w", "24x40/16w"};
 
 void pre_rb_shape(int c, const GridDesc& g, const GridDesc& gc, const float* xin, float* xout,
                   const float* b, const float* m, float* bc, double omega, int zero_init,
@@ -1005,7 +1005,9 @@ void pre_rb_shape(int c, const GridDesc& g, const GridDesc& gc, const float* xin
     case 1: pre_restrict_rb<20, 32, 8>(g, gc, xin, xout, b, m, bc, omega, zero_init, s); break;
     case 2: pre_restrict_rb<52, 32, 8>(g, gc, xin, xout, b, m, bc, omega, zero_init, s); break;
     case 3: pre_restrict_rb<52, 24, 8>(g, gc, xin, xout, b, m, bc, omega, zero_init, s); break;
-    default: pre_restrict_rb<20, 64, 8>(g, gc, xin, xout, b, m, bc, omega, zero_init, s); break;
+    case 4: pre_restrict_rb<20, 64, 8>(g, gc, xin, xout, b, m, bc, omega, zero_init, s); break;
+    case 5: pre_restrict_rb<20, 18, 8>(g, gc, xin, xout, b, m, bc, omega, zero_init, s); break;
+    default: pre_restrict_rb<20, 36, 16>(g, gc, xin, xout, b, m, bc, omega, zero_init, s); break;
   }
 }
 
@@ -1016,7 +1018,9 @@ void post_rb_shape(int c, const GridDesc& g, const GridDesc& gc, const float* xi
     case 1: prolong_post_rb<24, 24, 8>(g, gc, xin, xc, xout, b, m, omega, s); break;
     case 2: prolong_post_rb<56, 56, 16>(g, gc, xin, xc, xout, b, m, omega, s); break;
     case 3: prolong_post_rb<24, 48, 8>(g, gc, xin, xc, xout, b, m, omega, s); break;
-    default: prolong_post_rb<56, 24, 8>(g, gc, xin, xc, xout, b, m, omega, s); break;
+    case 4: prolong_post_rb<56, 24, 8>(g, gc, xin, xc, xout, b, m, omega, s); break;
+    case 5: prolong_post_rb<24, 16, 8>(g, gc, xin, xc, xout, b, m, omega, s); break;
+    default: prolong_post_rb<24, 40, 16>(g, gc, xin, xc, xout, b, m, omega, s); break;
   }
 }
 

