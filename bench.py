@@ -40,9 +40,32 @@ N_DEFAULT = 1025
 SOLVE_BYTES_PER_NODE_ITER = 2300.0
 
 # DRAM traffic per launch of the kernels the roofline may name (dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu capture of the 1025^2 mixed solve), valid while the
-# hashed source region of each kernel is unchanged.
-NCU_TRAFFIC = {}
+# dram__bytes_write.sum from one ncu capture, the average over the launches of that kernel
+# group), valid while the hashed source region of the kernels is unchanged. The middle-level
+# tiles: the pre- and post-smoothing launches on the 513^2, 257^2 and 129^2 levels (captured
+# in a 513^2 solve, whose tiled levels are exactly these and use the same tile shapes).
+NCU_TRAFFIC = {
+    "mid_level_tiles": {"bytes": (2116352 + 545792 + 152576 + 3456768 + 886272 + 242432) / 6.0,
+                        "source": ("paper_1806_05896_gb300/csrc/k_mg_fused.cu",
+                                   "// Register-blocked FP32 tile kernels",
+                                   "// One CTA, all coarse levels in shared memory"),
+                        "sha256": "00383ae4a950bfdd8fd27e2a90f8dd804e2c38663a5e0434477e27b72b020f46"},
+}
+
+
+def traffic_if_current(name):
+    """The recorded DRAM bytes per launch of a kernel group, or None once its source changed."""
+    import hashlib
+    t = NCU_TRAFFIC.get(name)
+    if not t:
+        return None
+    path, start, end = t["source"]
+    with open(os.path.join(ROOT, path)) as f:
+        src = f.read()
+    i, j = src.find(start), src.find(end)
+    if not 0 <= i < j or hashlib.sha256(src[i:j].encode()).hexdigest() != t["sha256"]:
+        return None
+    return t["bytes"]
 
 
 def rank_cells(rank: int, world: int, limit: int = 0) -> list:
@@ -511,10 +534,10 @@ def roofline_entry(kernels, hbm, peak_kind):
         return None
     k = kernels[0]
     achieved = k["achieved_gbs_pass"]
-    traffic = NCU_TRAFFIC.get(k["kernel"])
+    traffic = traffic_if_current(k["kernel"])
     return {"bound": "hbm", "kernel": KERNEL_NAMES.get(k["kernel"], k["kernel"]),
             "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": traffic["bytes"] if traffic else None, "peak_kind": peak_kind,
+            "traffic": traffic, "peak_kind": peak_kind,
             "algorithmic_bytes_per_launch": k["bytes_pass"],
             "avg_launch_us": k["avg_launch_us"], "sampled_launches": k["sampled_launches"],
             "per_launch_once": {"bytes": k["bytes_once"], "achieved": k["achieved_gbs_once"],

@@ -134,7 +134,9 @@ typedef struct {
                        cooperative launch per V-cycle instead of one launch per level (same
                        results to FP32 accuracy; fewer launches, no faster on GB300);
                        bit 8: mixed-precision MINRES without its FP64 iterative refinement;
-                       bit 9: no tile-shape autotuning (the fixed shapes of a timing sweep) */
+                       bit 9: no tile-shape autotuning (the fixed shapes of a timing sweep);
+                       bit 10: mixed FGMRES evaluates the saddle operator in FP64 instead of
+                       float-float */
 } ipm_options;
 
 typedef struct {
@@ -289,6 +291,13 @@ void ipm_server_destroy(ipm_server* sv);
  * Theta_y, Theta_w, Theta_v (Section 3). x, out: 4-field. */
 int ipm_newton_apply_device(ipm_solver* s, const double* theta_y, const double* theta_w,
                             const double* theta_v, const double* x, double* out);
+
+/* The same product evaluated as on the mixed-precision FGMRES path: in float-float
+ * arithmetic (two floats per value, about 2^-46 relative per operation) from shared-memory
+ * tiles, for the 2D Poisson problem without partial observation (IPM_EINVAL otherwise);
+ * the float-float result is returned as FP64 (high + low parts). */
+int ipm_newton_apply_ff_device(ipm_solver* s, const double* theta_y, const double* theta_w,
+                               const double* theta_v, const double* x, double* out);
 
 /* z = P^{-1} r for P_D (triangular = 0) or P_T (triangular = 1) built from the
  * given diagonals (Section 4), with the options' Chebyshev / multigrid settings

@@ -419,6 +419,73 @@ __global__ void k_newton_apply(GridDesc g, Stencil<double> st, IpmProblem pb, Ip
   }
 }
 
+// The same operator for the 2D Poisson problem in float-float arithmetic (FP32 pipes; this
+// GPU's FP64 rate is ~1/70 of its FP32 rate): a 32 x 8 block stages y, w - v and p of its
+// nodes and their one-node halo in shared memory, each FP64 value converted to float-float
+// once; the Q1 mass (rows [1 4 1] (x) [1 4 1] times h^2/36) and stiffness (3 x_c minus a
+// third of the 3 x 3 box) stencils, the Theta products and the combination run in float-float
+// (about 2^-46 relative per operation). Output: float-float Krylov vector planes.
+constexpr int kFFX = 32, kFFY = 8;
+__global__ void __launch_bounds__(kFFX * kFFY) k_newton_apply_ff2(GridDesc g, FF ms, FF third,
+                                                                 FF alpha,
+                                                                 const double* __restrict__ x,
+                                                                 const float* __restrict__ thyff,
+                                                                 const double* __restrict__ thw,
+                                                                 const double* __restrict__ thv,
+                                                                 float* __restrict__ out) {
+  constexpr int SX = kFFX + 2, SY = kFFY + 2;
+  __shared__ FF sy[SY][SX], sd[SY][SX], sp[SY][SX];
+  const long long F = g.field, p = g.pitch;
+  const int X0 = 1 + blockIdx.x * kFFX, Y0 = 1 + blockIdx.y * kFFY;
+  const int t = threadIdx.y * kFFX + threadIdx.x;
+  for (int q = t; q < SX * SY; q += kFFX * kFFY) {
+    const int lx = q % SX, ly = q / SX;
+    const int gx = X0 - 1 + lx, gy = Y0 - 1 + ly;
+    FF vy{0.f, 0.f}, vd{0.f, 0.f}, vp{0.f, 0.f};
+    if (gx < g.n && gy < g.n) {
+      const long long c = (long long)gy * p + gx;
+      vy = ff_from_double(x[c]);
+      vd = ff_from_double(x[F + c] - x[2 * F + c]);
+      vp = ff_from_double(x[3 * F + c]);
+    }
+    sy[ly][lx] = vy;
+    sd[ly][lx] = vd;
+    sp[ly][lx] = vp;
+  }
+  __syncthreads();
+  const int gx = X0 + threadIdx.x, gy = Y0 + threadIdx.y;
+  if (gx > g.n - 2 || gy > g.n - 2) return;
+  const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
+  auto four = [](FF a) { return FF{4.f * a.h, 4.f * a.l}; };
+  auto mass = [&](FF (*a)[SX]) {
+    auto row = [&](int r) { return ff_add(ff_add(a[r][lx - 1], four(a[r][lx])), a[r][lx + 1]); };
+    return ff_mul(ms, ff_add(ff_add(row(ly - 1), four(row(ly))), row(ly + 1)));
+  };
+  auto stiff = [&](FF (*a)[SX]) {
+    auto row = [&](int r) { return ff_add(ff_add(a[r][lx - 1], a[r][lx]), a[r][lx + 1]); };
+    const FF box = ff_add(ff_add(row(ly - 1), row(ly)), row(ly + 1));
+    const FF xc = a[ly][lx];
+    // 3 x_c as 2 x_c + x_c: scaling by 2 is exact, by 3 is not
+    return ff_add(ff_add(FF{2.f * xc.h, 2.f * xc.l}, xc), ff_neg(ff_mul(third, box)));
+  };
+  const long long c = (long long)gy * p + gx;
+  const FF My = mass(sy), Mp = mass(sp), Md = mass(sd), Ky = stiff(sy), Kp = stiff(sp);
+  const FF ty{thyff[c], thyff[F + c]};
+  const FF aMd = ff_mul(alpha, Md);
+  const FF r0 = ff_add(ff_add(My, ff_mul(ty, sy[ly][lx])), Kp);
+  const FF r1 = ff_add(ff_add(aMd, ff_mul(ff_from_double(thw[c]), ff_from_double(x[F + c]))),
+                       ff_neg(Mp));
+  const FF r2 = ff_add(ff_add(ff_neg(aMd), ff_mul(ff_from_double(thv[c]),
+                                                   ff_from_double(x[2 * F + c]))), Mp);
+  const FF r3 = ff_add(Ky, ff_neg(Md));
+  const FF r[4] = {r0, r1, r2, r3};
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    out[b * F + c] = r[b].h;
+    out[4 * F + b * F + c] = r[b].l;
+  }
+}
+
 // M_hat (and FP32 copies) from given diagonals, as in k_prep
 __global__ void k_mhat(GridDesc g, double alpha, double dM, const double* __restrict__ thy,
                        const double* __restrict__ thw, const double* __restrict__ thv,
@@ -546,4 +613,25 @@ void launch_to_float2(const GridDesc& g, const double* a, const double* b, float
                       cudaStream_t s) {
   count_launches(1);
   k_to_float2<<<interior_grid(g), interior_block(), 0, s>>>(g, a, b, a32, b32);
+}
+
+static FF ff_from_double_host(double v) {
+  const float h = (float)v;
+  return FF{h, (float)(v - (double)h)};
+}
+
+bool newton_apply_ff2_ok(const GridDesc& g, const IpmProblem& pb) {
+  return g.dim == 2 && !g.heat && !g.obs && pb.L.coef == nullptr;
+}
+
+void launch_newton_apply_ff2(const GridDesc& g, const IpmProblem& pb, const IpmDiag& dg,
+                             const double* x, float* y, cudaStream_t s) {
+  const double h2 = g.h * g.h / 36.0;
+  const int m = g.n - 2;
+  dim3 grid((m + kFFX - 1) / kFFX, (m + kFFY - 1) / kFFY);
+  count_launches(1);
+  k_newton_apply_ff2<<<grid, dim3(kFFX, kFFY), 0, s>>>(g, ff_from_double_host(h2),
+                                                        ff_from_double_host(1.0 / 3.0),
+                                                        ff_from_double_host(pb.alpha), x,
+                                                        dg.thyff, dg.thw, dg.thv, y);
 }

@@ -66,6 +66,11 @@ void launch_residuals(const GridDesc& g, const IpmProblem& pb, const IpmBounds& 
 void launch_newton_apply(const GridDesc& g, const IpmProblem& pb, const IpmDiag& dg,
                          const double* x, double* y, cudaStream_t s);
 // same operator, output as a float-float Krylov vector (high parts, then low parts)
+// the saddle operator evaluated in float-float arithmetic from shared-memory tiles (2D
+// Poisson without an observation mask only: newton_apply_ff2_ok); float-float output planes
+bool newton_apply_ff2_ok(const GridDesc& g, const IpmProblem& pb);
+void launch_newton_apply_ff2(const GridDesc& g, const IpmProblem& pb, const IpmDiag& dg,
+                             const double* x, float* y, cudaStream_t s);
 void launch_newton_apply_ff(const GridDesc& g, const IpmProblem& pb, const IpmDiag& dg,
                             const double* x, float* y, cudaStream_t s);
 long long interior_blocks(const GridDesc& g);

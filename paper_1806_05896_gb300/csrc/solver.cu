@@ -875,6 +875,7 @@ struct ipm_solver {
   // process (kernel_flags bit 9 keeps the fixed shapes). Runs eagerly, before any capture,
   // on this solver's level buffers, which the following cycle overwrites.
   bool autotune = true;
+  bool ff_operator = true;  // mixed FGMRES: saddle operator in float-float (kernel_flags bit 10)
   void autotune_tiles() {
     const int lc = coarse_start(mg32);
     for (int l = 0; l < lc; ++l) {
@@ -1201,7 +1202,10 @@ struct ipm_solver {
     int p1 = ph_begin(6);
     const double ob = 11.0 * 8.0 * (double)nI();
     int pr = prof_begin_kind(3, 16, ob, ob);
-    launch_newton_apply_ff(g, problem(), dg, zj, w, stream);
+    if (ff_operator && newton_apply_ff2_ok(g, problem()))
+      launch_newton_apply_ff2(g, problem(), dg, zj, w, stream);
+    else
+      launch_newton_apply_ff(g, problem(), dg, zj, w, stream);
     prof_end(pr);
     ph_end(p1);
     int p2 = ph_begin(7);
@@ -1573,6 +1577,7 @@ struct ipm_solver {
     use_graphs = (o.kernel_flags & 2) == 0;
     use_mid_cycle = (o.kernel_flags & 128) != 0;
     autotune = (o.kernel_flags & 512) == 0;
+    ff_operator = (o.kernel_flags & 1024) == 0;
   }
 
   int solve(const ipm_options& o, ipm_report* rep) {
@@ -1947,6 +1952,27 @@ int ipm_newton_apply_device(ipm_solver* s, const double* ty, const double* tw, c
     for (int b = 0; b < 4; ++b) launch_pack(s->g, x + b * m, s->rhs + b * f, 1, s->stream);
     s->newton_apply(s->rhs, s->dx);
     for (int b = 0; b < 4; ++b) launch_unpack(s->g, s->dx + b * f, nullptr, out + b * m, s->stream);
+    s->sync();
+    return IPM_OK;
+  });
+}
+
+int ipm_newton_apply_ff_device(ipm_solver* s, const double* ty, const double* tw,
+                               const double* tv, const double* x, double* out) {
+  if (!s || !ty || !tw || !tv || !x || !out) return IPM_EINVAL;
+  return guarded(s, [&] {
+    if (!newton_apply_ff2_ok(s->g, s->problem()))
+      throw IpmError{IPM_EINVAL, "the float-float operator covers 2D Poisson without observation"};
+    long long f = s->F(), m = s->nn();
+    launch_pack(s->g, ty, s->dg.thy, 1, s->stream);
+    launch_pack(s->g, tw, s->dg.thw, 1, s->stream);
+    launch_pack(s->g, tv, s->dg.thv, 1, s->stream);
+    launch_to_ff(s->dg.thyff, s->dg.thy, 1.0, f, s->stream);  // high plane, then low plane
+    for (int b = 0; b < 4; ++b) launch_pack(s->g, x + b * m, s->rhs + b * f, 1, s->stream);
+    float* ff = reinterpret_cast<float*>(s->dx);  // 8 f floats: high parts, then low parts
+    launch_newton_apply_ff2(s->g, s->problem(), s->dg, s->rhs, ff, s->stream);
+    launch_from_ff(s->ktmp, ff, 4 * f, s->stream);
+    for (int b = 0; b < 4; ++b) launch_unpack(s->g, s->ktmp + b * f, nullptr, out + b * m, s->stream);
     s->sync();
     return IPM_OK;
   });

@@ -34,7 +34,7 @@ EXPORTED = (
     "ipm_profile_smoother", "ipm_profile_read", "ipm_profile_phases", "ipm_profile_kernel",
     "ipm_profile_kernel_read", "ipm_tuning_report", "ipm_tuning_set", "ipm_set_observation",
     "ipm_strerror", "ipm_last_error",
-    "ipm_newton_apply_device", "ipm_precond_apply_device", "ipm_chebyshev_device",
+    "ipm_newton_apply_device", "ipm_newton_apply_ff_device", "ipm_precond_apply_device", "ipm_chebyshev_device",
     "ipm_vcycle_device", "ipm_newton_step_device", "ipm_chebyshev_noalloc",
     "ipm_reset", "ipm_device_bytes", "ipm_server_create", "ipm_server_submit",
     "ipm_server_wait", "ipm_server_stats", "ipm_server_destroy",
@@ -129,6 +129,7 @@ def load() -> C.CDLL:
     lib.ipm_last_error.argtypes = [P]
     lib.ipm_last_error.restype = C.c_char_p
     lib.ipm_newton_apply_device.argtypes = [P, P, P, P, P, P]
+    lib.ipm_newton_apply_ff_device.argtypes = [P, P, P, P, P, P]
     lib.ipm_precond_apply_device.argtypes = [P, C.POINTER(Options), C.c_int, P, P, P, P, P]
     lib.ipm_chebyshev_device.argtypes = [P, C.c_int, P, P, P]
     lib.ipm_vcycle_device.argtypes = [P, C.POINTER(Options), C.c_int, P, P, P]
@@ -425,9 +426,9 @@ class Solver:
     # ------------------------------------------------------------------
     # component entry points (torch CUDA float64 tensors)
     # ------------------------------------------------------------------
-    def newton_apply(self, th_y, th_w, th_v, x, out):
-        self._check(self._lib.ipm_newton_apply_device(self._h, _dptr(th_y), _dptr(th_w),
-                                                      _dptr(th_v), _dptr(x), _dptr(out)))
+    def newton_apply(self, th_y, th_w, th_v, x, out, float_float: bool = False):
+        fn = self._lib.ipm_newton_apply_ff_device if float_float else self._lib.ipm_newton_apply_device
+        self._check(fn(self._h, _dptr(th_y), _dptr(th_w), _dptr(th_v), _dptr(x), _dptr(out)))
         return out
 
     def precond_apply(self, triangular: bool, th_y, th_w, th_v, r, z, options=None, **kw):

@@ -60,6 +60,30 @@ def test_newton_apply_matches_oracle(dim, n, kind):
     s.close()
 
 
+@pytest.mark.parametrize("n", [5, 33, 65, 257, 1025])
+def test_newton_apply_float_float_matches_oracle(n):
+    """The float-float saddle operator of the mixed FGMRES path (2D Poisson): element-wise
+    within 2e-13 of |A| |x|: each float-float operation rounds at about 2^-46 = 1.4e-14
+    relative to its operands, and a row adds about a dozen terms (Theta spans eight orders
+    of magnitude here)."""
+    torch = torch_cuda()
+    qp = _qp(2, n)
+    rng = np.random.default_rng(n + 7)
+    th = _thetas(qp.nI, rng)
+    x = rng.standard_normal(4 * qp.nI)
+    A = oipm.newton_matrix(qp, *th)
+    ref = A @ x
+    s = _solver(qp)
+    out = torch.empty(4 * n * n, dtype=torch.float64, device="cuda")
+    s.newton_apply(*[dev(embed(qp, t)) for t in th], dev(embed4(qp, x)), out, float_float=True)
+    got = interior4(qp, host(out))
+    absA = abs(A) @ np.abs(x)
+    assert np.max(np.abs(got - ref) / absA) < 2e-13
+    full = host(out).reshape(4, -1)
+    assert np.all(full[:, fem.boundary_mask(2, n)] == 0.0)
+    s.close()
+
+
 @pytest.mark.parametrize("dim,n", [(2, 5), (2, 33), (2, 65), (3, 9), (3, 17)])
 def test_chebyshev_matches_oracle(dim, n):
     torch = torch_cuda()

@@ -16,7 +16,8 @@ def _mix():
     reqs = []
     for i, (dim, n, kind) in enumerate([(2, 33, "poisson"), (2, 65, "poisson"), (2, 33, "cd"),
                                         (2, 65, "cd"), (3, 9, "poisson"), (3, 17, "poisson"),
-                                        (2, 129, "poisson"), (2, 65, "poisson")]):
+                                        (2, 129, "poisson"), (2, 65, "poisson"),
+                                        (2, 257, "poisson"), (2, 257, "cd")]):
         rng = np.random.default_rng(100 + i)
         half = float(rng.uniform(1, 50))
         reqs.append(dict(dim=dim, n=n, kind=kind, eps=1.0 / 50.0,
