@@ -464,7 +464,7 @@ def run_ours(args, rank, world):
     }
     if rank == 0 and not args.no_extra:
         line["other_configs"] = other_configs(ipm, W, np)
-        line["serving"] = serving(ipm, W, np, args.serve_requests)
+        line["serving"] = serving(ipm, W, np, args.serve_requests, args.serve_workers)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -586,14 +586,14 @@ def other_configs(ipm, W, np):
     return out
 
 
-def serving(ipm, W, np, num):
+def serving(ipm, W, np, num, workers=16):
     """Seeded request stream (2D 65..513, 3D 33..65, 70/30 Poisson/CD) through the native
     server: a closed-loop burst (saturation throughput), then open loops at 0.8x and 1.5x that
     rate (exponential gaps), p50/p99 latency from submission to completion."""
     reqs = W.serving_stream(num, seed=0)
     opts = dict(precision=ipm.PREC_MIXED, stop=ipm.STOP_KKT, kkt_tol=1e-6, common_step=1,
                 max_ipm=60, restart=30)
-    sv = ipm.Server(workers=4, budget_bytes=96 << 30)
+    sv = ipm.Server(workers=workers, budget_bytes=96 << 30)
 
     def submit(r):
         return sv.submit(r["dim"], r["n"], r["alpha"], r["beta"], r["ua"], r["ub"], r["yd"],
@@ -608,7 +608,7 @@ def serving(ipm, W, np, num):
     res = [sv.wait(t) for t in tickets]
     burst_s = time.perf_counter() - t0
     sat = num / burst_s
-    out = {"requests": num, "workers": 4,
+    out = {"requests": num, "workers": workers,
            "saturation": {"solves_per_s": sat, "p50_ms": 1000 * pct([x[2] for x in res], 50),
                           "p99_ms": 1000 * pct([x[2] for x in res], 99),
                           "converged": sum(x[0]["kkt_rel"] <= 1e-6 for x in res)}}
@@ -733,6 +733,7 @@ def main():
                     help="ipm_options.kernel_flags of the timed solves (profiler runs pin the "
                          "tile shapes with 512: timings under a profiler mislead the autotuner)")
     ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-workers", type=int, default=16)
     ap.add_argument("--sweep-table", default="",
                     help="comma-separated grid sizes: print a sweep table and exit")
     ap.add_argument("--recipe", default="gauss", choices=["gauss", "poisson", "cd", "sparsity"])

@@ -165,7 +165,9 @@ int ipm_reset(ipm_solver* s, double alpha, double beta, const ipm_bounds* bounds
 size_t ipm_device_bytes(const ipm_solver* s);
 
 /* Use an existing CUDA stream (cudaStream_t passed as void*; NULL = the
- * solver's own stream). All device work of later calls is ordered on it. */
+ * solver's own stream). All device work of later calls is ordered on it. When the
+ * stream changes, the call first waits on the host for the work already enqueued on
+ * the previous one. Returns IPM_ECUDA if that wait reports an error. */
 int ipm_set_stream(ipm_solver* s, void* cuda_stream);
 
 int ipm_set_observation(ipm_solver* s, const double* lo, const double* hi);

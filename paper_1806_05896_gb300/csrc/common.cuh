@@ -13,23 +13,25 @@
 #define IPM_HD __host__ __device__ __forceinline__
 #define IPM_D __device__ __forceinline__
 
+// Every member has a default so that a descriptor filled in field by field never carries
+// stack contents into a kernel (the heat and observation members select stencil branches).
 struct GridDesc {
-  int dim;          // 2 or 3
-  int n;            // nodes per direction, boundary included
-  int pitch;        // elements per row
-  long long plane;  // elements per z-plane (pitch * n)
-  long long field;  // elements per field (plane for 2D, plane * n for 3D)
-  double h;         // mesh size 1/(n-1)
+  int dim = 2;          // 2 or 3
+  int n = 0;            // nodes per direction, boundary included
+  int pitch = 0;        // elements per row
+  long long plane = 0;  // elements per z-plane (pitch * n)
+  long long field = 0;  // elements per field (plane for 2D, plane * n for 3D)
+  double h = 0.0;       // mesh size 1/(n-1)
   // Space-time layout of the all-at-once heat equation (Section 3.4): a 2D grid of n^2
   // nodes per time level stored as the z-planes of a dim-3 grid, plane k = time t_k
   // (plane 0 the initial state, planes 1 .. n-2 the unknown levels, plane n-1 unused),
   // with the time-level masses tau M and the backward-Euler operator below.
-  int heat;         // 0, or 1 for the space-time layout
-  double tau;       // time step (heat layout)
+  int heat = 0;         // 0, or 1 for the space-time layout
+  double tau = 0.0;     // time step (heat layout)
   // Partial observation (the subsection on partial observations): per element, indexed by
   // the element's lowest-corner node, 1 where the tracking term integrates, else 0; null =
   // the whole domain. Only the tracking mass M_s of the state row uses it.
-  const float* obs;
+  const float* obs = nullptr;
 };
 
 IPM_HD long long node_index(const GridDesc& g, int i, int j, int k) {

@@ -6,9 +6,16 @@
 #include "kernels.h"
 #include <atomic>
 
+// process-wide total, and the calling thread's share (graph capture counts the launches it
+// records from the thread's share, which other host threads' solvers do not change)
 static std::atomic<long long> g_launches{0};
-void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static thread_local long long t_launches = 0;
+void count_launches(long long n) {
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  t_launches += n;
+}
 long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+long long launches_thread() { return t_launches; }
 
 namespace {
 

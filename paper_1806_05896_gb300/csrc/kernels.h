@@ -10,6 +10,7 @@
 // Number of kernel launches enqueued by this library since it was loaded.
 void count_launches(long long n);
 long long launches_total();
+long long launches_thread();
 
 // ----------------------------------------------------------------------------
 // Problem fields

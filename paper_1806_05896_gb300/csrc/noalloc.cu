@@ -106,6 +106,9 @@ extern "C" int ipm_chebyshev_noalloc(int dim, int n, int steps, const double* th
   g.plane = (long long)n * n;
   g.field = nodes;
   g.h = 1.0 / (n - 1);
+  g.heat = 0;  // the plain (stationary) stencil, whole-domain tracking
+  g.tau = 0.0;
+  g.obs = nullptr;
   double* bT = work;
   double* cur = work + nodes;
   double* prev = work + 2 * nodes;

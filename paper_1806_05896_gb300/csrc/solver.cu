@@ -140,10 +140,13 @@ struct ipm_solver {
       cudaGetLastError();
       throw IpmError{IPM_ENOMEM, "cudaMalloc of " + std::to_string(b) + " bytes failed"};
     }
-    CK(cudaMemset(p, 0, b));
     allocs.push_back(p);
     alloc_bytes.push_back(b);
     bytes += b;
+    // zeroed on the solver's stream: the streams are non-blocking, so a memset on the
+    // legacy stream would not be ordered before this solver's kernels (buffers are also
+    // allocated in the middle of a solve, when the Krylov basis grows)
+    CK(cudaMemsetAsync(p, 0, b, stream));
     return (T*)p;
   }
   void prof_flush() {
@@ -1282,7 +1285,7 @@ struct ipm_solver {
     }
     if (!gexec[j] && gruns[j] >= 1) {
       cudaGraph_t graph = nullptr;
-      long long before = launches_total();
+      long long before = launches_thread();
       CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
       try {
         arnoldi_body(o, j, stride, len, tri);
@@ -1292,13 +1295,13 @@ struct ipm_solver {
         cudaStreamEndCapture(stream, &partial);
         if (partial) cudaGraphDestroy(partial);
         cudaGetLastError();
-        count_launches(before - launches_total());
+        count_launches(before - launches_thread());
         throw;
       }
       CK(cudaStreamEndCapture(stream, &graph));
       // captured launches do not run now: count them at each replay instead
       gcount.resize(j + 1, 0);
-      gcount[j] = launches_total() - before;
+      gcount[j] = launches_thread() - before;
       count_launches(-gcount[j]);
       cudaGraphExec_t ex = nullptr;
       cudaError_t e = cudaGraphInstantiate(&ex, graph, 0);
@@ -1750,7 +1753,14 @@ size_t ipm_device_bytes(const ipm_solver* s) { return s ? s->bytes : 0; }
 
 int ipm_set_stream(ipm_solver* s, void* stream) {
   if (!s) return IPM_EINVAL;
-  s->stream = stream ? (cudaStream_t)stream : s->own;
+  cudaStream_t next = stream ? (cudaStream_t)stream : s->own;
+  // work already enqueued on the previous stream (zeroing of new buffers, an unfinished
+  // device-pointer call) completes before anything enqueued on the next one
+  if (next != s->stream && cudaStreamSynchronize(s->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return IPM_ECUDA;
+  }
+  s->stream = next;
   return IPM_OK;
 }
 

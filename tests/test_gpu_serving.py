@@ -83,3 +83,29 @@ def test_server_respects_memory_budget():
         sv.submit(2, 1025, 1e-2, 1e-3, -1.0, 1.0, big, **OPTS)
     assert e.value.code == ipm.ENOMEM
     sv.close()
+
+
+def test_server_many_workers_fresh_solvers_each_request():
+    """16 workers, every request on a grid key of its own (convection-diffusion with its own
+    eps), so solvers are created, zeroed and grown while the other workers' kernels run: each
+    result equals the request solved alone, bit for bit."""
+    torch_cuda()
+    reqs = []
+    for i in range(32):
+        rng = np.random.default_rng(500 + i)
+        n = (33, 65, 129)[i % 3]
+        half = float(rng.uniform(1, 50))
+        reqs.append(dict(dim=2, n=n, kind="cd" if i % 4 else "poisson", eps=1.0 / (20.0 + i),
+                         alpha=float(10 ** rng.uniform(-6, -2)),
+                         beta=float(10 ** rng.uniform(-5, -2)), ua=-half, ub=half,
+                         yd=W.yd_gaussian_sum(n, 500 + i, dim=2)))
+    alone = [_alone(r) for r in reqs]
+    sv = ipm.Server(workers=16, budget_bytes=32 << 30)
+    tickets = [sv.submit(r["dim"], r["n"], r["alpha"], r["beta"], r["ua"], r["ub"], r["yd"],
+                         kind=r["kind"], eps=r["eps"], **OPTS) for r in reqs]
+    for (rep_a, u_a), t in zip(alone, tickets):
+        rep, u, _, _ = sv.wait(t)
+        assert rep["status"] == rep_a["status"]
+        assert rep["ipm_iters"] == rep_a["ipm_iters"]
+        assert np.array_equal(u, u_a)
+    sv.close()
