@@ -595,9 +595,9 @@ def serving(ipm, W, np, num, workers=16):
                 max_ipm=60, restart=30)
     sv = ipm.Server(workers=workers, budget_bytes=96 << 30)
 
-    def submit(r):
+    def submit(r, o=opts):
         return sv.submit(r["dim"], r["n"], r["alpha"], r["beta"], r["ua"], r["ub"], r["yd"],
-                         kind=r["kind"], eps=r["eps"], sigma=r["sigma"], **opts)
+                         kind=r["kind"], eps=r["eps"], sigma=r["sigma"], **o)
     seen = {}
     for r in reqs:  # warm: one request per distinct grid and state equation
         seen.setdefault((r["dim"], r["n"], r["kind"]), r)
@@ -623,6 +623,16 @@ def serving(ipm, W, np, num, workers=16):
         dt = time.perf_counter() - t0
         out[f"open_loop_{load}x"] = {"offered_per_s": load * sat, "solves_per_s": num / dt,
                                      "p50_ms": 1000 * pct(lat, 50), "p99_ms": 1000 * pct(lat, 99)}
+    # the same stream prefix in mixed precision and all-FP64, closed loop, same server
+    head = reqs[:min(num, 128)]
+    for name, prec in (("mixed", ipm.PREC_MIXED), ("fp64", ipm.PREC_FP64)):
+        o = dict(opts, precision=prec)
+        t0 = time.perf_counter()
+        res = [sv.wait(t) for t in [submit(r, o) for r in head]]
+        dt = time.perf_counter() - t0
+        out.setdefault("precision_same_stream", {"requests": len(head)})[name] = {
+            "solves_per_s": len(head) / dt,
+            "converged": sum(x[0]["kkt_rel"] <= 1e-6 for x in res)}
     sv.close()
     out["mix"] = ("2D {65,129,257,513}^2, 3D {33,65}^3, Poisson/CD 70/30 (CD 2D only), "
                   "log-uniform alpha, beta, Gaussian-sum y_d, mixed precision, kkt_rel 1e-6")

@@ -452,22 +452,75 @@ IPM_D void coarse_cycle_box(const MGCoarse<T>& cl, const T* __restrict__ btop,
   // and the current-iterate parity of every level as a register bit mask: indexing
   // per-thread arrays by the runtime level index would put them in local memory
   __shared__ int s_n[kMaxCoarse], s_off[kMaxCoarse];  // (per kernel, shared with coarse_cycle)
+  __shared__ int s_pre[kMaxCoarse + 1];  // interior nodes of the levels before level l
   if (threadIdx.x == 0) {
-    int off = 0;
+    int off = 0, pre = 0;
     for (int l = 0; l < cl.nl; ++l) {
       s_n[l] = cl.n[l];
       s_off[l] = off;
+      s_pre[l] = pre;
       off += 6 * cl.n[l] * cl.n[l];
+      pre += (cl.n[l] - 2) * (cl.n[l] - 2);
     }
+    s_pre[cl.nl] = pre;
   }
   __syncthreads();
   const int total = s_off[cl.nl - 1] + 6 * s_n[cl.nl - 1] * s_n[cl.nl - 1];
   auto arr = [&](int l, int a) { return base + s_off[l] + a * s_n[l] * s_n[l]; };
   enum { AX0 = 0, AX1 = 1, AB = 2, AR = 3, AM = 4, AJ = 5 };
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
+  if constexpr (sizeof(T) == 4) {
+    // FP32: the interior nodes of all levels as one flat range, kSlots per thread, so that
+    // every global load of a thread is in flight at once (and behind the zeroing of the
+    // shared arrays) instead of one level and one row at a time
+    constexpr int kSlots = 6;
+    const int nint = s_pre[cl.nl];
+    for (int t0 = 0; t0 < nint; t0 += kSlots * (int)blockDim.x) {
+      T vm[kSlots], vb[kSlots], vx[kSlots];
+      int dst[kSlots], lev[kSlots];
+#pragma unroll
+      for (int k = 0; k < kSlots; ++k) {
+        const int t = t0 + k * (int)blockDim.x + (int)threadIdx.x;
+        lev[k] = -1;
+        vm[k] = vb[k] = vx[k] = T(0);
+        dst[k] = 0;
+        if (t < nint) {
+          int l = 0;
+          while (t >= s_pre[l + 1]) ++l;
+          const int w = s_n[l] - 2, r = t - s_pre[l];
+          const int iy = 1 + r / w, ix = 1 + r - (iy - 1) * w;
+          lev[k] = l;
+          dst[k] = iy * s_n[l] + ix;
+          vm[k] = cl.m[l][(long long)iy * cl.pitch[l] + ix];
+          if (l == 0) {
+            vb[k] = btop[(long long)iy * cl.pitch[0] + ix];
+            if (load_x) vx[k] = xtop[(long long)iy * cl.pitch[0] + ix];
+          }
+        }
+      }
+      if (t0 == 0) {
+        for (int t = threadIdx.x; t < total; t += blockDim.x) base[t] = T(0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < kSlots; ++k) {
+        const int l = lev[k];
+        if (l < 0) continue;
+        arr(l, AM)[dst[k]] = vm[k];
+        arr(l, AJ)[dst[k]] = omega / (T(8.0 / 3.0) + vm[k]);
+        if (l == 0) {
+          arr(0, AB)[dst[k]] = vb[k];
+          if (load_x) arr(0, AX0)[dst[k]] = vx[k];
+        }
+      }
+    }
+    if (nint == 0) {
+      for (int t = threadIdx.x; t < total; t += blockDim.x) base[t] = T(0);
+    }
+  } else {
   // zero everything, then load b (top level) and m (all levels), interior entries
   for (int t = threadIdx.x; t < total; t += blockDim.x) base[t] = T(0);
   __syncthreads();
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
   for (int l = 0; l < cl.nl; ++l) {
     const int n = s_n[l];
     T* Ml = arr(l, AM);
@@ -482,6 +535,7 @@ IPM_D void coarse_cycle_box(const MGCoarse<T>& cl, const T* __restrict__ btop,
         if (l == 0) arr(0, AB)[iy * n + ix] = btop[(long long)iy * cl.pitch[0] + ix];
         if (l == 0 && load_x) arr(0, AX0)[iy * n + ix] = xtop[(long long)iy * cl.pitch[0] + ix];
       }
+  }
   }
   __syncthreads();
   unsigned cur = 0;  // bit l: level l's current iterate is x1
