@@ -521,7 +521,8 @@ KERNEL_NAMES = {
                            "residual + restriction)",
     "finest_prolong_post": "k_mg2_prolong_post_rb<56,32,5,8> (finest level: prolongation + 5 sweeps)",
     "coarse_cycle": "k_mg2_coarse<float> (one-CTA V-cycle on the levels 65^2 ... 3^2)",
-    "saddle_operator": "k_newton_apply (FP64 saddle operator of (NewtonSystem))",
+    "saddle_operator": "k_newton_apply_ff2 / k_newton_apply (saddle operator of (NewtonSystem): "
+                       "float-float on the Arnoldi path, FP64 for the true residuals)",
     "mid_level_tiles": "k_mg2_pre_restrict_rb<20,32,5,8> / k_mg2_prolong_post_rb<24,24,5,8> "
                        "(levels 513^2 ... 129^2)",
 }
