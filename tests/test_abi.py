@@ -83,3 +83,33 @@ def test_server_wait_returns_the_solves_own_error(lib):
         assert e.value.code in want
     finally:
         sv.close()
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every public struct the binding passes through the ABI has the header's size and field
+    offsets (compiled with the host C compiler against include/ipm.h)."""
+    import ctypes
+    pairs = [("ipm_grid", ipm.Grid), ("ipm_pde", ipm.Pde), ("ipm_bounds", ipm.Bounds),
+             ("ipm_options", ipm.Options), ("ipm_report", ipm.Report),
+             ("ipm_request", ipm.Request)]
+    lines = []
+    for cname, cls in pairs:
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"ipm.h\"\n"
+                   "int main(void) {\n" + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                        str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = {}
+    for line in out.splitlines():
+        cname, field, value = line.split()
+        got[(cname, field)] = int(value)
+    for cname, cls in pairs:
+        assert ctypes.sizeof(cls) == got[(cname, "sizeof")], cname
+        for field, _ in cls._fields_:
+            assert getattr(cls, field).offset == got[(cname, field)], (cname, field)
