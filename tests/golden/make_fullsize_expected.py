@@ -7,8 +7,8 @@ benchmark), and the final iterate is sampled:
 
 * ``grid``  -- the values of y, u, p on every ``stride``-th node in each direction
   (boundary included), a coarse copy that covers the whole domain;
-* ``patch`` -- a dense block of consecutive nodes in the middle of the domain (2D) or a
-  dense plane (3D), for the fine-scale structure;
+* ``patch`` -- a dense block of consecutive nodes in the middle of the domain (2D) or three
+  consecutive dense planes (3D), for the fine-scale structure;
 * ``norm_*`` -- the 2-norms of the full nodal vectors;
 * ``k``, ``mu``, ``kkt_rel`` -- iteration count, barrier parameter and the oracle's kkt_rel.
 
@@ -38,7 +38,7 @@ CASES = {
     "poisson2d_1025_cell1": (lambda: W.workload_c2(n=1025, cell=1), "gmg", 8, (448, 512)),
     "poisson2d_1025_cell3": (lambda: W.workload_c2(n=1025, cell=3), "gmg", 8, (448, 512)),
     "cd2d_513": (lambda: W.workload_c4(n=513), "lu", 4, (224, 288)),
-    "poisson3d_65": (lambda: W.workload_c3(n=65), "gmg", 4, (32, 33)),
+    "poisson3d_65": (lambda: W.workload_c3(n=65), "gmg", 4, (31, 34)),
 }
 
 

@@ -10,7 +10,8 @@ stored files themselves, independently of both the oracle and the GPU path:
 * y, u, p vanish on the boundary (zero Dirichlet data, interior unknowns), the control lies
   strictly inside its box and the state below its bound (interior-point iterates);
 * the full vectors' norms bound the norms of any subset of their entries;
-* on the dense 2D patch, the discrete state equation L y - M u = f (Section 2) holds at
+* on the dense patch (a block in 2D, three planes in 3D), the discrete state equation
+  L y - M u = f (Section 2) holds at
   every node whose stencil lies inside the patch, within the primal residual that the stored
   kkt_rel allows: |(f - L y + M u)_i| <= ||xi_p||_2 <= kkt_rel (1 + ||f|| + ||M y_d||).
   That bound is rigorous but loose (the stored iterates meet it with a factor 1e-9 to
@@ -95,14 +96,14 @@ def test_stored_values_respect_boundary_box_and_norms(name):
         assert np.linalg.norm(d[f + "_patch"]) <= nf * (1 + 1e-14)
 
 
-@pytest.mark.parametrize("name", [c for c in CASES if G.CASES[c][0]().dim == 2])
+@pytest.mark.parametrize("name", CASES)
 def test_stored_patch_satisfies_the_state_equation(name):
     make, _inner, _stride, patch = G.CASES[name]
     wl = make()
     d = _load(name)
     qp = Q.from_workload(wl)
     n = wl.n
-    nn = n * n
+    nn = n ** wl.dim
     pidx = d["patch_idx"]
     y = np.zeros(nn)
     u = np.zeros(nn)
@@ -124,7 +125,10 @@ def test_stored_patch_satisfies_the_state_equation(name):
         if known[cols].all():
             rows.append(r)
     rows = np.array(rows)
-    assert rows.size >= (patch[1] - patch[0] - 2) ** 2 // 2
+    # the patch's interior: (width - 2)^2 nodes in 2D, one full plane's interior in 3D
+    want = (patch[1] - patch[0] - 2) ** 2 if wl.dim == 2 else \
+        (patch[1] - patch[0] - 2) * (n - 2) ** 2
+    assert rows.size == want
     f_full = np.zeros(nn)
     f_full[qp.idx] = qp.fvec
     resid = f_full[rows] - (A[rows] @ y - B[rows] @ u)
