@@ -116,3 +116,30 @@ def test_heat_rejects_what_it_does_not_cover():
     with pytest.raises(ipm.IpmError):
         s.solve(krylov=ipm.KRYLOV_MINRES_PD)
     s.close()
+
+
+# 33^2 with 31 time levels: expected values written by the oracle's iterative tier
+# (tests/golden/make_heat_expected.py; the direct tier at this size takes many minutes)
+@pytest.mark.parametrize("prec,bar", [(ipm.PREC_FP64, 1e-8), (ipm.PREC_MIXED, 1e-6)])
+def test_heat_33_matches_oracle_iterative_tier(prec, bar):
+    import os
+    import workloads as W
+    torch_cuda()
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "heat_33.npz")
+    ref = dict(np.load(path))
+    n, T, k = int(ref["n"]), float(ref["T"]), int(ref["k"])
+    d = W.heat_moving_target(n, T)
+    s = ipm.Solver(2, n, float(ref["alpha"]), float(ref["beta"]), float(ref["ua"]),
+                   float(ref["ub"]), kind="heat", T=T)
+    s.set_data(d["yd3"], None, d["g3"])
+    rep = s.solve(stop=ipm.STOP_FIXED, fixed_iters=k, sigma=float(ref["sigma"]),
+                  krylov=ipm.KRYLOV_GMRES_PT, precision=prec,
+                  krylov_tol=1e-12 if prec == ipm.PREC_FP64 else 1e-10)
+    got = dict(y=s.state().reshape(-1), u=s.control().reshape(-1), p=s.adjoint().reshape(-1))
+    hist = s.history()
+    s.close()
+    assert rep["ipm_iters"] == k
+    assert hist[-1]["mu"] == pytest.approx(float(ref["mu"]), rel=1e-12)
+    for f in ("y", "u", "p"):
+        assert rel(got[f], ref[f]) < bar, (f, rel(got[f], ref[f]))
+    assert abs(hist[-1]["kkt_rel"] - float(ref["kkt_rel"])) <= 1e-2 * float(ref["kkt_rel"])

@@ -78,3 +78,23 @@ def test_fgmres_solves_a_nonsymmetric_system_exactly():
     x, st = iterative.fgmres(A, b, prec, tol=1e-13, restart=7)
     assert st.relres <= 1e-13
     assert _rel(x, np.linalg.solve(A, b)) < 1e-12
+
+
+@pytest.mark.parametrize("n,k", [(9, 8), (17, 6)])
+def test_iterative_tier_matches_direct_tier_on_the_heat_equation(n, k):
+    """The all-at-once heat problem (Section 3.4; calL block bidiagonal in time, so P_T's
+    inner solves use the exact LU of calL + M_hat): both tiers give the same iterates."""
+    from oracle import heat
+    T = 0.5
+    d = W.heat_moving_target(n, T)
+    qp = heat.build_heat(n, n - 2, T, 1e-2, 1e-3, -2.0, 1.5, yd=d["yd"], y0=d["y0"])
+    rd = ipm.solve(qp, sigma=0.25, n_iter=k)
+    stats = []
+    ri = ipm.solve(qp, sigma=0.25, n_iter=k,
+                   newton_solve=iterative.newton_solver("lu", stats=stats))
+    assert len(stats) == k and max(s.relres for s in stats) < 1e-10
+    assert _rel(ri.u(), rd.u()) < 1e-11
+    assert _rel(ri.state.y, rd.state.y) < 1e-11
+    assert _rel(ri.state.p, rd.state.p) < 1e-11
+    for a, b in zip(ri.history, rd.history):
+        assert a["mu"] == b["mu"]

@@ -12,6 +12,7 @@ from .generators import (  # noqa: F401
     yd_cd_bump,
     poisson_2d_sweep,
     serving_stream,
+    heat_moving_target,
     Workload,
     workload_c1,
     workload_c2,

@@ -63,6 +63,29 @@ def yd_cd_bump(n: int) -> np.ndarray:
     return np.exp(-64.0 * ((x - 0.5) ** 2 + (y - 0.5) ** 2))
 
 
+def heat_moving_target(n: int, T: float) -> dict:
+    """Inputs of an all-at-once heat-equation problem with n - 2 time levels on [0, T]:
+    a desired state sin(pi x) sin(pi y) (1 + 2t) cos(2 pi t) at t_k = k T / (n - 2),
+    k = 1 .. n - 2, and the initial state 0.5 sin(pi x) sin(2 pi y) (zero on the boundary).
+    Returned per level (``yd``: (n - 2, n^2), ``y0``: n^2) and in the space-time layout of an
+    n^3 array whose plane k is time level k (``yd3``: planes 1 .. n - 2; ``g3``: plane 0 =
+    y0, the rest zero)."""
+    nt = n - 2
+    tau = T / nt
+    x, y = node_coords(2, n)
+    x, y = x.reshape(-1), y.reshape(-1)
+    base = np.sin(np.pi * x) * np.sin(np.pi * y)
+    yd = np.stack([base * (1.0 + 2.0 * (k + 1) * tau) * np.cos(2.0 * np.pi * (k + 1) * tau)
+                   for k in range(nt)])
+    y0 = 0.5 * np.sin(np.pi * x) * np.sin(2.0 * np.pi * y)
+    edge = (x == 0.0) | (x == 1.0) | (y == 0.0) | (y == 1.0)
+    yd3 = np.zeros((n, n * n))
+    yd3[1:n - 1] = yd
+    g3 = np.zeros((n, n * n))
+    g3[0] = np.where(edge, 0.0, y0)
+    return dict(yd=yd, y0=y0, yd3=yd3.reshape(-1), g3=g3.reshape(-1), nt=nt, tau=tau)
+
+
 @dataclasses.dataclass
 class Workload:
     """One optimal control problem instance (inputs only)."""
