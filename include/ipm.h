@@ -99,9 +99,13 @@ enum { IPM_STOP_PAPER = 0, IPM_STOP_KKT = 1, IPM_STOP_FIXED = 2 };
  * Krylov tolerance 1e-10 (relative unpreconditioned residual), 20 Chebyshev
  * steps, 3 V-cycles with 5 pre- and 5 post-smoothing steps.
  *   precision: IPM_PREC_FP64 everywhere, or IPM_PREC_MIXED (Chebyshev and
- *              multigrid in FP32; Krylov recurrences, operator and IPM in FP64;
- *              GMRES is then flexible GMRES, and MINRES runs inside an FP64
- *              iterative refinement loop that restores krylov_tol on the true residual).
+ *              multigrid in FP32; the IPM, the true residuals and the Krylov scalars in
+ *              FP64; GMRES is then flexible GMRES, and for 2D Poisson without partial
+ *              observation its Arnoldi basis, orthogonalisation and saddle operator use
+ *              float-float arithmetic (two floats per value, about 2^-46 relative per
+ *              operation; kernel_flags bits 5 and 10 select FP64 instead); MINRES runs
+ *              inside an FP64 iterative refinement loop that restores krylov_tol on the
+ *              true residual).
  *   krylov:    IPM_KRYLOV_MINRES_PD (MINRES + P_D) or IPM_KRYLOV_GMRES_PT
  *              (GMRES + P_T, right-preconditioned, flexible form).
  *   stop:      IPM_STOP_PAPER: ||xi_p|| <= eps_p, ||xi_d|| <= eps_d, ||xi_c|| <= eps_c
@@ -150,8 +154,10 @@ typedef struct {
 
 void ipm_default_options(ipm_options* opt);
 
-/* Create a solver for one problem; allocates all device memory on the current
- * CUDA device. beta >= 0, alpha > 0. On success *out owns the solver. */
+/* Create a solver for one problem on the current CUDA device: allocates the nodal
+ * fields, both multigrid hierarchies and the solver's own stream; the Krylov basis is
+ * allocated by the first solve that needs it (and grows with a larger restart).
+ * beta >= 0, alpha > 0. On success *out owns the solver. */
 int ipm_create(const ipm_grid* grid, const ipm_pde* pde, double alpha, double beta,
                const ipm_bounds* bounds, ipm_solver** out);
 
